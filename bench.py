@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Layered-field benchmark.
+
+One bench step = one tessellation job on the 512 x 512 jittered planar grid
+(262,144 vertices, 1024 seeds, FP32 field): lf_seed, 2000 time-iterations
+(lf_step) and the sharp labels (lf_labels).  The metric is nnz-updates/s: the
+interest-skeleton entries advanced per second, summed over the job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own jobs on its own GPU (independent jobs,
+no data-path collective: weak scaling); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+job on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "field nnz-updates/s and HBM GB/s (% of peak) vs plain; p50/p99 job latency"
+UNIT = "nnz-updates/s"
+
+WORKLOADS = {
+    "grid512": dict(desc="planar grid 512x512, alternating diagonals, jitter U(-0.2,0.2) (stream 2), "
+                         "1024 seeds (stream 3), FP32 field, 2000 time steps",
+                    mesh=lambda: synth.planar_grid(512, jitter=0.2, seed=2), k=1024, seed_stream=3,
+                    steps=2000, dtype="f32"),
+    "torus1024": dict(desc="noisy torus R=1 r=0.35 on a 1024x1024 grid, 4-octave value noise amp 0.02 "
+                           "(stream 4), 8192 seeds (stream 5), FP32 field, 3000 time steps",
+                      mesh=lambda: synth.noisy_torus(1024), k=8192, seed_stream=5, steps=3000, dtype="f32"),
+    "ico3": dict(desc="icosphere level 3 (642 vertices), 16 seeds (stream 1), FP32 field, 300 time steps",
+                 mesh=lambda: synth.icosphere(3), k=16, seed_stream=1, steps=300, dtype="f32"),
+}
+
+# DRAM bytes of one step-kernel launch from an ncu capture of the grid512
+# workload, valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def kernel_sha():
+    p = os.path.join(ROOT, "paper_1804_09152_gb300", "csrc", "lf_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(wl, n_steps):
+    """The FP64 oracle on the first n_steps time steps of the job."""
+    import oracle
+    m = wl["mesh"]()
+    L = oracle.cotan_laplacian(m.V, m.F)
+    F = oracle.seed(m.n_v, synth.sample_seeds(m.n_v, wl["k"], wl["seed_stream"]))
+    units = 0
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        F, sk = oracle.step(L, F)
+        units += sk
+    dt = time.perf_counter() - t0
+    return units, dt
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample_steps = args.ref_sample_steps
+    vals = []
+    for i in range(args.warmup + args.steps):
+        units, dt = oracle_sample(wl, sample_steps)
+        if i >= args.warmup:
+            vals.append((units, dt))
+    units = sum(u for u, _ in vals)
+    secs = sum(d for _, d in vals)
+    value = units / secs
+    sample = f"first {sample_steps} of {wl['steps']} time steps of the job per bench step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(vals),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "desc": wl["desc"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import torch
+    import paper_1804_09152_gb300 as pkg
+    pkg.build()
+    from paper_1804_09152_gb300 import _lib as lf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    m = wl["mesh"]()
+    seeds = synth.sample_seeds(m.n_v, wl["k"], wl["seed_stream"])
+    T = wl["steps"]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    with torch.cuda.stream(stream):
+        dev = lf.torch_device(stream)
+        mesh = lf.Mesh(m.V, m.F, device=dev, field_dtype=wl["dtype"])
+
+        def job():
+            mesh.seed(seeds)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+            mesh.step(T)
+            e2.record(stream)
+            lab = mesh.labels()
+            return e1, e2, lab
+
+        for _ in range(args.warmup):
+            job()
+        stats0 = mesh.stats()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        job_ms, step_ms, units, io, retries = [], [], 0, 0, 0
+        wall0 = time.perf_counter()
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                flush.zero_()                          # evict L2 between jobs
+                torch.cuda.synchronize()
+                s0 = mesh.stats()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e3 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                e1, e2, lab = job()
+                e3.record(stream)
+                e3.synchronize()
+                s1 = mesh.stats()
+                job_ms.append(e0.elapsed_time(e3))
+                step_ms.append(e1.elapsed_time(e2))
+                units += s1["skeleton_total"]
+                io += s1["nnz_io_total"]
+                retries += s1["retries"]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - wall0
+        st = mesh.stats()
+
+    t_job = sum(job_ms) / 1e3
+    if dist:
+        t = torch.tensor([t_job], device="cuda")
+        u = torch.tensor([float(units)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        t_all, units_all = float(t.item()), float(u.item())
+    else:
+        t_all, units_all = t_job, float(units)
+    value = units_all / t_all
+
+    # roofline of the step kernel: algorithmic bytes (ideal reuse) per launch
+    vb = st["value_bytes"]
+    launches = args.steps * T
+    bytes_L = 4 * (m.n_v + 1) + 8 * st["operator_nnz"]
+    bytes_total = launches * (bytes_L + 2 * 4 * (m.n_v + 1)) + (2 + vb) * io
+    t_step = sum(step_ms) / 1e3
+    achieved = bytes_total / t_step / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel_sha"] == kernel_sha() else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_total / launches,
+                "us_per_launch": 1e6 * t_step / launches}
+
+    # end to end through the C ABI from host buffers: create (host cotan build +
+    # upload), seed, steps, labels back to the host, destroy
+    e2e_units, e2e_t = 0, 0.0
+    n_e2e = max(1, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        for _ in range(n_e2e):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mm = lf.Mesh(m.V, m.F, device=lf.torch_device(stream), field_dtype=wl["dtype"])
+            mm.seed(seeds)
+            mm.step(T)
+            lab = mm.labels()
+            s = mm.stats()
+            mm.close()
+            torch.cuda.synchronize()
+            e2e_t += time.perf_counter() - t0
+            e2e_units += s["skeleton_total"]
+    h2d = 4 * (m.n_v + 1) + 8 * st["operator_nnz"] + 4 * wl["k"]
+    d2h = 4 * m.n_v
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(job_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n_v": m.n_v, "n_f": m.n_f,
+                   "seeds": wl["k"], "time_steps_per_job": T, "l2": "flushed between jobs (512 MiB write)",
+                   "working_set_bytes": int(bytes_L + 2 * (4 * (m.n_v + 1) + (2 + vb) * st["capacity"])),
+                   "lloyd_and_dual": "not part of this line"},
+        "latency_ms": {"p50": float(np.percentile(job_ms, 50)), "p99": float(np.percentile(job_ms, 99))},
+        "roofline": roofline,
+        "e2e": {"value": e2e_units / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "jobs": n_e2e},
+        "gpu_launches": args.steps * (T + 3) + retries,
+        "clocks": clk.summary(),
+        "wall_s": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        units_c, dt_c = oracle_sample(wl, args.cpu_sample_steps)
+        line["cpu_baseline"] = {"value": units_c / dt_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {args.cpu_sample_steps} of {T} time steps of one job "
+                                          f"({dt_c:.1f} s, literal Algorithm 1, single thread)"}
+    mesh.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="grid512")
+    ap.add_argument("--cpu-sample-steps", type=int, default=200)
+    ap.add_argument("--ref-sample-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * lf.h -- C ABI of the GB300 layered-field library.
+ *
+ * Layered fields (Zayer, Mlakar, Steinberger, Seidel, "Layered Fields for
+ * Natural Tessellations on Surfaces", arXiv 1804.09152) partition a triangle
+ * mesh into cells by growing one field per seed concurrently.  The field is a
+ * sparse (vertex x layer) matrix F: row i lists the layers present at vertex
+ * i with their values in (0, 1].  Layers 0..k-1 belong to the k seeds, layer
+ * k is the base layer (Sec. 3.1).  One time-iteration (Algorithm 1) multiplies
+ * the mesh Laplacian with F, evaluates the interest skeleton, applies the
+ * explicit Euler update with clamping (Eq. 11-13) and normalises every vertex
+ * (Sec. 4); this library runs that iteration as one fused CUDA kernel per step.
+ *
+ * Conventions for every function below.
+ *  - Host arrays passed in are owned by the caller and are copied (or fully
+ *    consumed) before the call returns.
+ *  - Output arrays are allocated by the caller; a call that fills one waits
+ *    for the mesh's stream to finish.
+ *  - Device memory is owned by the mesh handle.  It is allocated through the
+ *    lf_device hooks when given, else with cudaMalloc, and released by
+ *    lf_destroy_mesh.
+ *  - No C++ exception crosses this interface and nothing aborts the process.
+ *    Every function returns an lf_status; lf_last_error() gives a message.
+ *  - After LF_ERR_CUDA or LF_ERR_TIMEOUT a handle is poisoned: later calls on
+ *    it return LF_ERR_STATE.  Other errors leave the handle usable.
+ *  - A handle is not thread-safe.  Distinct handles may be used from distinct
+ *    threads on distinct streams.
+ *  - Kernels run on the stream given in lf_device (0 = legacy default stream).
+ */
+#ifndef LF_H
+#define LF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LF_OK = 0,
+  LF_ERR_INVALID = 1,   /* bad argument; nothing was changed                  */
+  LF_ERR_OOM = 2,       /* device allocation failed; state unchanged          */
+  LF_ERR_CUDA = 3,      /* a CUDA call failed; the handle is poisoned         */
+  LF_ERR_TIMEOUT = 4,   /* a bounded device wait gave up; handle poisoned     */
+  LF_ERR_STATE = 5,     /* call not valid in this state (e.g. step before seed,
+                           or a poisoned handle)                              */
+  LF_ERR_CAPACITY = 6   /* a size limit of the library was exceeded           */
+} lf_status;
+
+/* Storage type of the field values.  All arithmetic is FP32. */
+typedef enum { LF_F32 = 0, LF_BF16 = 1, LF_F16 = 2 } lf_dtype;
+
+/*
+ * Parameters of the update (Algorithm 1; Eq. 2, 11-13; Sec. 7).
+ * The coefficient matrices w, a, e of Algorithm 1 are given by two classes of
+ * layer pairs: two seed layers ("cell-cell", _cc) and a seed layer with the
+ * base layer ("cell-base", _cb).  w and a are symmetric; e is not: e_cb is the
+ * entry in a cell's row against the base, e_bc the entry in the base row.
+ * A layer has no coefficient with itself.  lf_default_params() fills
+ *   dt = 5 (Sec. 7), mu = 1, w_cc = 0.2, a_cc = a_cb = 0.04 (w = 0.2 and a
+ *   factor 5 between w and a, Sec. 3.1), w_cb = 0, e_cc = 0, e_cb = 0.5,
+ *   e_bc = -0.5 (Eq. 12 is antisymmetric in the pair), iso = 0.25 (Sec. 5.1),
+ *   field_dtype = LF_F32, initial_capacity = 0.
+ * initial_capacity: entries each field buffer holds before the first growth;
+ *   0 picks max(2 n_v, 4096).  Growth is automatic (lf_step), so this only
+ *   trades memory against re-runs of a step.
+ */
+typedef struct {
+  double dt;
+  double mu;
+  double w_cc, w_cb;
+  double a_cc, a_cb;
+  double e_cc, e_cb, e_bc;
+  double iso;
+  int32_t field_dtype;   /* lf_dtype */
+  int32_t reserved;      /* must be 0 */
+  int64_t initial_capacity;
+} lf_params;
+
+/*
+ * Device context.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  alloc/free, when both non-NULL, replace cudaMalloc/cudaFree for
+ * every device buffer of a handle: alloc(bytes, cuda_stream, user) returns a
+ * device pointer aligned to 256 bytes or NULL; free(ptr, user) releases it.
+ * The struct is copied by lf_create_mesh; the hooks must stay callable until
+ * lf_destroy_mesh returns.
+ */
+typedef struct {
+  void* cuda_stream;
+  void* (*alloc)(size_t bytes, void* cuda_stream, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} lf_device;
+
+typedef struct lf_mesh_s* lf_mesh;
+
+typedef struct {
+  int64_t n_v;            /* vertices                                         */
+  int64_t n_layers;       /* k + 1 after lf_seed, else 0                       */
+  int64_t steps;          /* time-iterations completed since lf_seed           */
+  int64_t nnz;            /* entries of the current field                      */
+  int64_t capacity;       /* entries each field buffer can hold                */
+  int64_t operator_nnz;   /* off-diagonal entries of L (diagonal is implicit)  */
+  uint64_t skeleton_total;/* sum over completed steps of |interest skeleton|    */
+  uint64_t nnz_io_total;  /* sum over completed steps of nnz(in) + nnz(out)     */
+  int64_t device_bytes;   /* device memory held by the handle                  */
+  int32_t retries;        /* steps re-run after a capacity or map overflow     */
+  int32_t map_slots;      /* per-vertex layer-union slots of the step kernel   */
+  int32_t field_dtype;    /* lf_dtype                                          */
+  int32_t value_bytes;    /* bytes per stored field value                      */
+} lf_stats_t;
+
+/* Defaults listed at lf_params. */
+void lf_default_params(lf_params* p);
+
+/*
+ * Builds the static operator of a triangle mesh: the cotangent Laplacian
+ * (precomputed once, Sec. 3.2), L_ij = (cot alpha_ij + cot beta_ij) / 2 over
+ * the angles opposite edge ij, L_ii = -sum_j L_ij, no mass matrix; every edge
+ * is kept even when its weight is 0.  Computed in FP64 on the host, stored on
+ * the device as FP32 CSR without the diagonal.
+ *   V: n_v x 3 doubles, row-major.  F: n_f x 3 int32 vertex ids, 0-based.
+ *   params: copied; may be NULL for the defaults.
+ * Errors: LF_ERR_INVALID for n_v < 3, n_v >= 2^31, n_f < 1, an id out of
+ * range, a repeated id in a face or a zero-area face, or invalid params
+ * (dt <= 0, mu < 0, unknown dtype); LF_ERR_OOM; LF_ERR_CUDA.  *out is set
+ * only on LF_OK.
+ */
+lf_status lf_create_mesh(const lf_device* dev, const double* V, int64_t n_v,
+                         const int32_t* F, int64_t n_f, const lf_params* params,
+                         lf_mesh* out);
+
+/*
+ * Same with a caller-given symmetric operator instead of the cotangent
+ * Laplacian (the paper leaves the discretisation open).  CSR over n_v rows:
+ * rowptr (n_v + 1, int64), col (int32, sorted per row), val (double).
+ * Diagonal entries are ignored: the library always uses L_ii = -sum_j L_ij.
+ * Errors as lf_create_mesh, plus LF_ERR_INVALID for a non-monotone rowptr or
+ * a column out of range.
+ */
+lf_status lf_create_mesh_csr(const lf_device* dev, int64_t n_v, const int64_t* rowptr,
+                             const int32_t* col, const double* val,
+                             const lf_params* params, lf_mesh* out);
+
+/*
+ * Initialisation (Algorithm 1, first line; Sec. 3.1-3.2): seed s (0 <= s < k)
+ * gets value 1 in layer s at vertex seed_vertices[s]; every other vertex gets
+ * value 1 in the base layer k.  Resets the step counter and statistics.
+ * Errors: LF_ERR_INVALID for k < 1, k + 1 > 65536, a vertex out of range or
+ * a repeated vertex.
+ */
+lf_status lf_seed(lf_mesh m, const int32_t* seed_vertices, int32_t k);
+
+/*
+ * Runs n_iters time-iterations of Algorithm 1 (the body of its time loop):
+ * L_t = L F (the paper's Phi L^T for a symmetric L), the interest skeleton
+ * irows_i = {l : F_il > 0} u {l : F_il = 0, (L F)_il > 0}, the explicit Euler
+ * update of Eq. 11-13 over the skeleton with clamping to [0, 1], the
+ * normalisation of every vertex to sum 1 and the removal of zero entries
+ * (Sec. 4).  Every d uses the values before the step.  Returns after the
+ * work is done on the device.  When a field buffer or the per-vertex layer
+ * union overflows, the library grows it (by at least 20 %, Sec. 4) and re-runs
+ * the step; results do not depend on it.
+ * Errors: LF_ERR_STATE before lf_seed; LF_ERR_INVALID for n_iters < 0;
+ * LF_ERR_OOM when growth fails (the field stays at the last completed step);
+ * LF_ERR_CAPACITY when a vertex sees more layers than the library supports;
+ * LF_ERR_TIMEOUT, LF_ERR_CUDA.
+ */
+lf_status lf_step(lf_mesh m, int32_t n_iters);
+
+/*
+ * Sharp labels (Sec. 6: the field of largest value at each vertex).
+ * labels[i] = layer of the largest value at vertex i, the lowest layer id on
+ * a tie, and -1 when that layer is the base layer.  labels: n_v int32.
+ * maxval: NULL or n_v floats receiving that largest value.
+ * Errors: LF_ERR_STATE before lf_seed.
+ */
+lf_status lf_labels(lf_mesh m, int32_t* labels, float* maxval);
+
+/*
+ * Copies the current field to the host as CSR: rowptr (n_v + 1 int64),
+ * layer (int32), val (float, widened from the storage type).  With layer or
+ * val NULL, or cap smaller than the number of entries, only *nnz and rowptr
+ * (if non-NULL) are written and LF_OK is returned: a size query.
+ */
+lf_status lf_get_field(lf_mesh m, int64_t* rowptr, int32_t* layer, float* val,
+                       int64_t cap, int64_t* nnz);
+
+/*
+ * Replaces the current field (checkpoint resume, tests).  Same layout as
+ * lf_get_field; values are rounded to the storage type.  n_layers = k + 1.
+ * Errors: LF_ERR_INVALID for a non-monotone rowptr, a layer out of range or
+ * not strictly increasing within a row, a value not in (0, 1] or not finite,
+ * n_layers < 2 or > 65536.
+ */
+lf_status lf_set_field(lf_mesh m, const int64_t* rowptr, const int32_t* layer,
+                       const float* val, int64_t nnz, int32_t n_layers);
+
+/* Counters of the handle; see lf_stats_t. */
+lf_status lf_stats(lf_mesh m, lf_stats_t* out);
+
+/* Releases the handle and all its device memory (waits for its stream). */
+void lf_destroy_mesh(lf_mesh m);
+
+/* Static string for a status code. */
+const char* lf_status_string(lf_status s);
+
+/* Message of the last failed call on m (m = NULL: last failed create). */
+const char* lf_last_error(lf_mesh m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LF_H */

@@ -1,0 +1,264 @@
+"""ctypes binding of the C ABI in ``include/lf.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+layered-field arithmetic: the work runs in ``_build/liblf.so``.  Importing this
+module raises if the library has not been built; there is no fallback.
+
+Device memory and streams may come from PyTorch: ``torch_device()`` returns an
+``lf_device`` that allocates through the caching allocator of the current
+device and runs on its current stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .native import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(f"CUDA library {LIB} is missing: run paper_1804_09152_gb300.build() first")
+
+_lib = ctypes.CDLL(LIB)
+
+LF_OK, LF_ERR_INVALID, LF_ERR_OOM, LF_ERR_CUDA, LF_ERR_TIMEOUT, LF_ERR_STATE, LF_ERR_CAPACITY = range(7)
+LF_F32, LF_BF16, LF_F16 = 0, 1, 2
+DTYPES = {"f32": LF_F32, "bf16": LF_BF16, "f16": LF_F16}
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class lf_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("mu", ctypes.c_double),
+                ("w_cc", ctypes.c_double), ("w_cb", ctypes.c_double),
+                ("a_cc", ctypes.c_double), ("a_cb", ctypes.c_double),
+                ("e_cc", ctypes.c_double), ("e_cb", ctypes.c_double), ("e_bc", ctypes.c_double),
+                ("iso", ctypes.c_double),
+                ("field_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("initial_capacity", ctypes.c_int64)]
+
+
+class lf_device(ctypes.Structure):
+    _fields_ = [("cuda_stream", ctypes.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN),
+                ("user", ctypes.c_void_p)]
+
+
+class lf_stats_t(ctypes.Structure):
+    _fields_ = [("n_v", ctypes.c_int64), ("n_layers", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("capacity", ctypes.c_int64), ("operator_nnz", ctypes.c_int64),
+                ("skeleton_total", ctypes.c_uint64), ("nnz_io_total", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_int64), ("retries", ctypes.c_int32), ("map_slots", ctypes.c_int32),
+                ("field_dtype", ctypes.c_int32), ("value_bytes", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_lib.lf_default_params.argtypes = [ctypes.POINTER(lf_params)]
+_lib.lf_default_params.restype = None
+_lib.lf_create_mesh.argtypes = [ctypes.POINTER(lf_device), _P, _i64, _P, _i64, ctypes.POINTER(lf_params),
+                                ctypes.POINTER(_P)]
+_lib.lf_create_mesh.restype = ctypes.c_int
+_lib.lf_create_mesh_csr.argtypes = [ctypes.POINTER(lf_device), _i64, _P, _P, _P, ctypes.POINTER(lf_params),
+                                    ctypes.POINTER(_P)]
+_lib.lf_create_mesh_csr.restype = ctypes.c_int
+_lib.lf_seed.argtypes = [_P, _P, _i32]
+_lib.lf_seed.restype = ctypes.c_int
+_lib.lf_step.argtypes = [_P, _i32]
+_lib.lf_step.restype = ctypes.c_int
+_lib.lf_labels.argtypes = [_P, _P, _P]
+_lib.lf_labels.restype = ctypes.c_int
+_lib.lf_get_field.argtypes = [_P, _P, _P, _P, _i64, ctypes.POINTER(_i64)]
+_lib.lf_get_field.restype = ctypes.c_int
+_lib.lf_set_field.argtypes = [_P, _P, _P, _P, _i64, _i32]
+_lib.lf_set_field.restype = ctypes.c_int
+_lib.lf_stats.argtypes = [_P, ctypes.POINTER(lf_stats_t)]
+_lib.lf_stats.restype = ctypes.c_int
+_lib.lf_destroy_mesh.argtypes = [_P]
+_lib.lf_destroy_mesh.restype = None
+_lib.lf_status_string.argtypes = [ctypes.c_int]
+_lib.lf_status_string.restype = ctypes.c_char_p
+_lib.lf_last_error.argtypes = [_P]
+_lib.lf_last_error.restype = ctypes.c_char_p
+
+EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_step", "lf_labels",
+            "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error"]
+
+
+class LFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_lib.lf_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+def _check(status, mesh=None):
+    if status != LF_OK:
+        raise LFError(status, _lib.lf_last_error(mesh).decode(errors="replace"))
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_P)
+
+
+def lf_default_params(**overrides):
+    p = lf_params()
+    _lib.lf_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "field_dtype" and isinstance(v, str):
+            v = DTYPES[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def torch_device(stream=None):
+    """lf_device running on a torch stream with torch's caching allocator."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    dev_index = s.device.index if s.device.index is not None else torch.cuda.current_device()
+
+    def _alloc(nbytes, cuda_stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev_index, s)
+        except Exception:
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    d = lf_device()
+    d.cuda_stream = s.cuda_stream
+    d.alloc = _ALLOC_FN(_alloc)
+    d.free = _FREE_FN(_free)
+    d.user = None
+    d._keep = (d.alloc, d.free, s)      # the callbacks must outlive the mesh
+    return d
+
+
+def lf_create_mesh(V, F, params=None, device=None):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    out = _P()
+    st = _lib.lf_create_mesh(ctypes.byref(device) if device is not None else None, _ptr(V), V.shape[0], _ptr(F),
+                             F.shape[0], ctypes.byref(params) if params is not None else None, ctypes.byref(out))
+    _check(st)
+    return out
+
+
+def lf_create_mesh_csr(rowptr, col, val, params=None, device=None):
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    out = _P()
+    st = _lib.lf_create_mesh_csr(ctypes.byref(device) if device is not None else None, rowptr.size - 1,
+                                 _ptr(rowptr), _ptr(col), _ptr(val),
+                                 ctypes.byref(params) if params is not None else None, ctypes.byref(out))
+    _check(st)
+    return out
+
+
+def lf_seed(mesh, seeds):
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    _check(_lib.lf_seed(mesh, _ptr(seeds), seeds.size), mesh)
+
+
+def lf_step(mesh, n_iters):
+    _check(_lib.lf_step(mesh, int(n_iters)), mesh)
+
+
+def lf_labels(mesh, n_v, with_max=False):
+    lab = np.empty(n_v, np.int32)
+    mx = np.empty(n_v, np.float32) if with_max else None
+    _check(_lib.lf_labels(mesh, _ptr(lab), _ptr(mx)), mesh)
+    return (lab, mx) if with_max else lab
+
+
+def lf_get_field(mesh, n_v):
+    """Returns (rowptr int64, layer int32, val float32)."""
+    nnz = _i64()
+    rp = np.empty(n_v + 1, np.int64)
+    _check(_lib.lf_get_field(mesh, _ptr(rp), None, None, 0, ctypes.byref(nnz)), mesh)
+    lay = np.empty(max(nnz.value, 1), np.int32)
+    val = np.empty(max(nnz.value, 1), np.float32)
+    _check(_lib.lf_get_field(mesh, _ptr(rp), _ptr(lay), _ptr(val), lay.size, ctypes.byref(nnz)), mesh)
+    return rp, lay[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+def lf_set_field(mesh, rowptr, layer, val, n_layers):
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    layer = np.ascontiguousarray(layer, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float32)
+    _check(_lib.lf_set_field(mesh, _ptr(rowptr), _ptr(layer), _ptr(val), layer.size, int(n_layers)), mesh)
+
+
+def lf_stats(mesh):
+    s = lf_stats_t()
+    _check(_lib.lf_stats(mesh, ctypes.byref(s)), mesh)
+    return s.as_dict()
+
+
+def lf_destroy_mesh(mesh):
+    _lib.lf_destroy_mesh(mesh)
+
+
+def lf_status_string(status):
+    return _lib.lf_status_string(status).decode()
+
+
+def lf_last_error(mesh=None):
+    return _lib.lf_last_error(mesh).decode(errors="replace")
+
+
+class Mesh:
+    """Owns one lf_mesh handle; each method calls the entry point of the same name."""
+
+    def __init__(self, V=None, F=None, params=None, device=None, csr=None, **overrides):
+        if params is None:
+            params = lf_default_params(**overrides)
+        self.params = params
+        self.device = device
+        if csr is not None:
+            self.n_v = len(csr[0]) - 1
+            self.h = lf_create_mesh_csr(*csr, params=params, device=device)
+        else:
+            self.n_v = int(np.asarray(V).shape[0])
+            self.h = lf_create_mesh(V, F, params=params, device=device)
+
+    def seed(self, seeds):
+        lf_seed(self.h, seeds)
+
+    def step(self, n):
+        lf_step(self.h, n)
+
+    def labels(self, with_max=False):
+        return lf_labels(self.h, self.n_v, with_max)
+
+    def get_field(self):
+        return lf_get_field(self.h, self.n_v)
+
+    def set_field(self, rowptr, layer, val, n_layers):
+        lf_set_field(self.h, rowptr, layer, val, n_layers)
+
+    def stats(self):
+        return lf_stats(self.h)
+
+    def close(self):
+        if self.h:
+            lf_destroy_mesh(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

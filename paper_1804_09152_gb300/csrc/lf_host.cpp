@@ -1,0 +1,730 @@
+// Host side of the layered-field library: mesh operator, device buffers,
+// the step driver (CUDA graphs, overflow recovery) and the C ABI of lf.h.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lf.h"
+#include "lf_internal.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kGraphSteps = 128;     // kernel nodes per captured graph
+constexpr int kPollSteps = 512;      // steps between status checks in lf_step
+constexpr int64_t kMaxCap = 2147483000LL;
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct lf_mesh_s {
+  lf_device dev{};
+  cudaStream_t stream = nullptr;
+  lf_params params{};
+  int64_t n_v = 0;
+  int64_t L_nnz = 0;
+  int dtype = 0;
+  int n_layers = 0;
+  int64_t cap = 0;
+  int num_tiles = 0;
+  int tier = 0;
+  int64_t steps = 0;
+  int retries = 0;
+  bool poisoned = false;
+  std::string err;
+  int64_t device_bytes = 0;
+  std::vector<Alloc> allocs;
+
+  int32_t* d_Lrp = nullptr;
+  int2* d_Lcv = nullptr;
+  lf::FieldBuf buf[2]{};
+  lf::DevStatus* d_st = nullptr;
+  unsigned long long* d_tiles = nullptr;
+  int tiles_alloc = 0;
+  lf::JobDesc* d_job = nullptr;
+  lf::JobDesc h_job{};
+  lf::DevStatus h_st{};
+  int32_t* d_labels = nullptr;
+  float* d_scratch_f = nullptr;
+  int64_t scratch_f_len = 0;
+
+  cudaGraphExec_t gexec = nullptr;
+  int graph_tier = -1;
+
+  ~lf_mesh_s() {
+    cudaStreamSynchronize(stream);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& a : allocs) release(a.p);
+  }
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (dev.alloc && dev.free) {
+      p = dev.alloc(bytes, dev.cuda_stream, dev.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) {
+      allocs.push_back({p, bytes});
+      device_bytes += static_cast<int64_t>(bytes);
+    }
+    return p;
+  }
+
+  void release(void* p) {
+    if (!p) return;
+    if (dev.alloc && dev.free) dev.free(p, dev.user);
+    else cudaFree(p);
+  }
+
+  void dfree(void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < allocs.size(); ++i) {
+      if (allocs[i].p == p) {
+        device_bytes -= static_cast<int64_t>(allocs[i].bytes);
+        allocs.erase(allocs.begin() + static_cast<std::ptrdiff_t>(i));
+        break;
+      }
+    }
+    release(p);
+  }
+};
+
+namespace {
+
+lf_status fail(lf_mesh m, lf_status s, const std::string& msg) {
+  if (m) m->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+lf_status cuda_fail(lf_mesh m, cudaError_t e, const char* where) {
+  if (m) m->poisoned = true;
+  return fail(m, LF_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LF_CUDA(m, call)                                    \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((m), e_, #call); \
+  } while (0)
+
+bool params_ok(const lf_params& p, std::string& why) {
+  if (!(p.dt > 0.0) || !std::isfinite(p.dt)) { why = "dt must be positive"; return false; }
+  if (!(p.mu >= 0.0) || !std::isfinite(p.mu)) { why = "mu must be >= 0"; return false; }
+  const double cs[] = {p.w_cc, p.w_cb, p.a_cc, p.a_cb, p.e_cc, p.e_cb, p.e_bc, p.iso};
+  for (double c : cs)
+    if (!std::isfinite(c)) { why = "coefficients must be finite"; return false; }
+  if (p.field_dtype < 0 || p.field_dtype > 2) { why = "unknown field_dtype"; return false; }
+  if (p.reserved != 0) { why = "reserved must be 0"; return false; }
+  if (p.initial_capacity < 0 || p.initial_capacity >= kMaxCap) { why = "initial_capacity out of range"; return false; }
+  return true;
+}
+
+// Cotangent weights: for the corner p of triangle (p, q, s), the edge (q, s)
+// receives cot(angle at p) / 2.  Returns false on a zero-area face.
+bool cotan_rows(int64_t n_v, const double* V, int64_t n_f, const int32_t* F,
+                std::vector<int64_t>& rp, std::vector<int32_t>& col, std::vector<double>& val,
+                std::string& why) {
+  std::vector<int64_t> start(static_cast<size_t>(n_v) + 1, 0);
+  for (int64_t f = 0; f < n_f; ++f)
+    for (int c = 0; c < 3; ++c) start[static_cast<size_t>(F[3 * f + c]) + 1] += 2;
+  for (int64_t i = 0; i < n_v; ++i) start[i + 1] += start[i];
+  std::vector<std::pair<int32_t, double>> ent(static_cast<size_t>(start[n_v]));
+  std::vector<int64_t> fill(start.begin(), start.end() - 1);
+  for (int64_t f = 0; f < n_f; ++f) {
+    const int32_t v[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+    for (int c = 0; c < 3; ++c) {
+      const int32_t p = v[c], q = v[(c + 1) % 3], s = v[(c + 2) % 3];
+      const double* P = V + 3 * static_cast<int64_t>(p);
+      const double* Q = V + 3 * static_cast<int64_t>(q);
+      const double* S = V + 3 * static_cast<int64_t>(s);
+      const double ux = Q[0] - P[0], uy = Q[1] - P[1], uz = Q[2] - P[2];
+      const double wx = S[0] - P[0], wy = S[1] - P[1], wz = S[2] - P[2];
+      const double cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+      const double twice_area = std::sqrt(cx * cx + cy * cy + cz * cz);
+      if (!(twice_area > 0.0) || !std::isfinite(twice_area)) {
+        why = "face " + std::to_string(f) + " has zero area";
+        return false;
+      }
+      const double half_cot = 0.5 * (ux * wx + uy * wy + uz * wz) / twice_area;
+      ent[static_cast<size_t>(fill[q]++)] = {s, half_cot};
+      ent[static_cast<size_t>(fill[s]++)] = {q, half_cot};
+    }
+  }
+  rp.assign(static_cast<size_t>(n_v) + 1, 0);
+  col.clear();
+  val.clear();
+  col.reserve(ent.size() / 2 + 16);
+  val.reserve(ent.size() / 2 + 16);
+  for (int64_t i = 0; i < n_v; ++i) {
+    auto b = ent.begin() + start[i], e = ent.begin() + start[i + 1];
+    std::stable_sort(b, e, [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+      return x.first < y.first;
+    });
+    for (auto it = b; it != e;) {
+      auto jt = it;
+      double w = 0.0;
+      while (jt != e && jt->first == it->first) { w += jt->second; ++jt; }
+      col.push_back(it->first);
+      val.push_back(w);
+      it = jt;
+    }
+    rp[static_cast<size_t>(i) + 1] = static_cast<int64_t>(col.size());
+  }
+  return true;
+}
+
+lf_status upload_job(lf_mesh m) {
+  LF_CUDA(m, cudaMemcpyAsync(m->d_job, &m->h_job, sizeof(lf::JobDesc), cudaMemcpyHostToDevice, m->stream));
+  return LF_OK;
+}
+
+lf_status read_status(lf_mesh m) {
+  LF_CUDA(m, cudaMemcpyAsync(&m->h_st, m->d_st, sizeof(lf::DevStatus), cudaMemcpyDeviceToHost, m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  return LF_OK;
+}
+
+// Clears the error state and the scan state after a failed step.
+lf_status reset_after_failure(lf_mesh m) {
+  lf::DevStatus s = m->h_st;
+  s.err = 0;
+  s.ticket = 0;
+  s.done = 0;
+  s.need_nnz = 0;
+  s.need_map = 0;
+  s.skeleton_step = 0;
+  m->h_st = s;
+  LF_CUDA(m, cudaMemcpyAsync(m->d_st, &s, sizeof(s), cudaMemcpyHostToDevice, m->stream));
+  LF_CUDA(m, cudaMemsetAsync(m->d_tiles, 0, sizeof(unsigned long long) * m->num_tiles, m->stream));
+  return LF_OK;
+}
+
+int tiles_for(int64_t n_v, int tier) {
+  const int b = lf::kTiers[tier].block;
+  return static_cast<int>((n_v + b - 1) / b);
+}
+
+// (Re)allocates the look-back words for the current tier.
+lf_status ensure_tiles(lf_mesh m) {
+  const int need = tiles_for(m->n_v, m->tier);
+  if (need > m->tiles_alloc) {
+    auto* p = static_cast<unsigned long long*>(m->dalloc(sizeof(unsigned long long) * need));
+    if (!p) return fail(m, LF_ERR_OOM, "allocating tile status");
+    m->dfree(m->d_tiles);
+    m->d_tiles = p;
+    m->tiles_alloc = need;
+  }
+  m->num_tiles = need;
+  m->h_job.num_tiles = need;
+  m->h_job.tile_status = m->d_tiles;
+  LF_CUDA(m, cudaMemsetAsync(m->d_tiles, 0, sizeof(unsigned long long) * need, m->stream));
+  return LF_OK;
+}
+
+// Grows both field buffers to new_cap entries, keeping the current field.
+lf_status grow_capacity(lf_mesh m, int64_t new_cap) {
+  if (new_cap > kMaxCap) return fail(m, LF_ERR_CAPACITY, "field exceeds 2^31 entries");
+  const int vb = lf::value_bytes(m->dtype);
+  const int cur = static_cast<int>(m->h_st.epoch & 1u);
+  int32_t nnz = 0;
+  if (m->buf[cur].ids) {
+    LF_CUDA(m, cudaMemcpyAsync(&nnz, m->buf[cur].rowptr + m->n_v, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               m->stream));
+    LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  }
+  void* ids[2] = {nullptr, nullptr};
+  void* vals[2] = {nullptr, nullptr};
+  for (int b = 0; b < 2; ++b) {
+    ids[b] = m->dalloc(sizeof(uint16_t) * static_cast<size_t>(new_cap));
+    vals[b] = m->dalloc(static_cast<size_t>(vb) * static_cast<size_t>(new_cap));
+    if (!ids[b] || !vals[b]) {
+      for (int c = 0; c <= b; ++c) { m->dfree(ids[c]); m->dfree(vals[c]); }
+      return fail(m, LF_ERR_OOM, "growing the field buffers");
+    }
+  }
+  if (nnz > 0 && m->buf[cur].ids) {
+    LF_CUDA(m, cudaMemcpyAsync(ids[cur], m->buf[cur].ids, sizeof(uint16_t) * nnz, cudaMemcpyDeviceToDevice,
+                               m->stream));
+    LF_CUDA(m, cudaMemcpyAsync(vals[cur], m->buf[cur].vals, static_cast<size_t>(vb) * nnz,
+                               cudaMemcpyDeviceToDevice, m->stream));
+  }
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  for (int b = 0; b < 2; ++b) {
+    m->dfree(m->buf[b].ids);
+    m->dfree(m->buf[b].vals);
+    m->buf[b].ids = static_cast<uint16_t*>(ids[b]);
+    m->buf[b].vals = vals[b];
+    m->h_job.buf[b] = m->buf[b];
+  }
+  m->cap = new_cap;
+  m->h_job.cap = static_cast<int32_t>(new_cap);
+  return upload_job(m);
+}
+
+lf_status build_graph(lf_mesh m) {
+  if (m->gexec && m->graph_tier == m->tier) return LF_OK;
+  if (m->gexec) {
+    cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+  }
+  size_t smem = 0;
+  const void* fn = lf::step_kernel(m->dtype, m->tier, &smem);
+  cudaGraph_t g = nullptr;
+  LF_CUDA(m, cudaGraphCreate(&g, 0));
+  void* args[1] = {&m->d_job};
+  cudaKernelNodeParams p{};
+  p.func = const_cast<void*>(fn);
+  p.gridDim = dim3(static_cast<unsigned>(m->num_tiles));
+  p.blockDim = dim3(static_cast<unsigned>(lf::kTiers[m->tier].block));
+  p.sharedMemBytes = static_cast<unsigned>(smem);
+  p.kernelParams = args;
+  cudaGraphNode_t prev = nullptr;
+  for (int s = 0; s < kGraphSteps; ++s) {
+    cudaGraphNode_t node = nullptr;
+    cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(m, e, "cudaGraphAddKernelNode");
+    }
+    prev = node;
+  }
+  cudaError_t e = cudaGraphInstantiate(&m->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(m, e, "cudaGraphInstantiate");
+  m->graph_tier = m->tier;
+  return LF_OK;
+}
+
+lf_status check_usable(lf_mesh m) {
+  if (!m) return fail(nullptr, LF_ERR_INVALID, "null mesh");
+  if (m->poisoned) return fail(m, LF_ERR_STATE, "handle is poisoned by an earlier CUDA error or timeout");
+  return LF_OK;
+}
+
+// Common tail of both create paths: off-diagonal FP64 CSR -> device.
+lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int64_t>& rp,
+                        const std::vector<int32_t>& col, const std::vector<double>& val,
+                        const lf_params& prm, lf_mesh* out) {
+  static bool kernels_ready = false;
+  if (!kernels_ready) {
+    cudaError_t e = lf::init_kernels();
+    if (e != cudaSuccess) return fail(nullptr, LF_ERR_CUDA, std::string("init_kernels: ") + cudaGetErrorString(e));
+    kernels_ready = true;
+  }
+  lf_mesh m = new (std::nothrow) lf_mesh_s();
+  if (!m) return fail(nullptr, LF_ERR_OOM, "host allocation");
+  if (dev) m->dev = *dev;
+  m->stream = static_cast<cudaStream_t>(m->dev.cuda_stream);
+  m->params = prm;
+  m->n_v = n_v;
+  m->dtype = prm.field_dtype;
+  const int64_t nnz = static_cast<int64_t>(col.size());
+  if (nnz >= kMaxCap) {
+    delete m;
+    return fail(nullptr, LF_ERR_CAPACITY, "operator exceeds 2^31 entries");
+  }
+  m->L_nnz = nnz;
+  std::vector<int32_t> rp32(static_cast<size_t>(n_v) + 1);
+  for (int64_t i = 0; i <= n_v; ++i) rp32[static_cast<size_t>(i)] = static_cast<int32_t>(rp[static_cast<size_t>(i)]);
+  std::vector<int2> cv(static_cast<size_t>(std::max<int64_t>(nnz, 1)));
+  for (int64_t q = 0; q < nnz; ++q) {
+    float w = static_cast<float>(val[static_cast<size_t>(q)]);
+    int bits;
+    std::memcpy(&bits, &w, 4);
+    cv[static_cast<size_t>(q)] = make_int2(col[static_cast<size_t>(q)], bits);
+  }
+  m->d_Lrp = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * (n_v + 1)));
+  m->d_Lcv = static_cast<int2*>(m->dalloc(sizeof(int2) * std::max<int64_t>(nnz, 1)));
+  m->d_st = static_cast<lf::DevStatus*>(m->dalloc(sizeof(lf::DevStatus)));
+  m->d_job = static_cast<lf::JobDesc*>(m->dalloc(sizeof(lf::JobDesc)));
+  for (int b = 0; b < 2; ++b) m->buf[b].rowptr = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * (n_v + 1)));
+  if (!m->d_Lrp || !m->d_Lcv || !m->d_st || !m->d_job || !m->buf[0].rowptr || !m->buf[1].rowptr) {
+    delete m;
+    return fail(nullptr, LF_ERR_OOM, "device allocation");
+  }
+  cudaError_t e = cudaMemcpyAsync(m->d_Lrp, rp32.data(), sizeof(int32_t) * (n_v + 1), cudaMemcpyHostToDevice,
+                                  m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_Lcv, cv.data(), sizeof(int2) * std::max<int64_t>(nnz, 1), cudaMemcpyHostToDevice,
+                        m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_st, 0, sizeof(lf::DevStatus), m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(nullptr, LF_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+  }
+  lf::JobDesc& j = m->h_job;
+  j.n_v = static_cast<int32_t>(n_v);
+  j.n_layers = 0;
+  j.L_rowptr = m->d_Lrp;
+  j.L_colval = m->d_Lcv;
+  j.buf[0] = m->buf[0];
+  j.buf[1] = m->buf[1];
+  j.st = m->d_st;
+  j.c = lf::Coefs{static_cast<float>(prm.dt),   static_cast<float>(prm.mu),   static_cast<float>(prm.w_cc),
+                  static_cast<float>(prm.w_cb), static_cast<float>(prm.a_cc), static_cast<float>(prm.a_cb),
+                  static_cast<float>(prm.e_cc), static_cast<float>(prm.e_cb), static_cast<float>(prm.e_bc)};
+  lf_status s = ensure_tiles(m);
+  if (s == LF_OK)
+    s = grow_capacity(m, prm.initial_capacity > 0 ? prm.initial_capacity : std::max<int64_t>(2 * n_v, 4096));
+  if (s == LF_OK) s = upload_job(m);
+  if (s != LF_OK) {
+    g_create_error = m->err;
+    delete m;
+    return s;
+  }
+  *out = m;
+  return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lf_default_params(lf_params* p) {
+  if (!p) return;
+  p->dt = 5.0;
+  p->mu = 1.0;
+  p->w_cc = 0.2;
+  p->w_cb = 0.0;
+  p->a_cc = 0.04;
+  p->a_cb = 0.04;
+  p->e_cc = 0.0;
+  p->e_cb = 0.5;
+  p->e_bc = -0.5;
+  p->iso = 0.25;
+  p->field_dtype = LF_F32;
+  p->reserved = 0;
+  p->initial_capacity = 0;
+}
+
+lf_status lf_create_mesh(const lf_device* dev, const double* V, int64_t n_v, const int32_t* F, int64_t n_f,
+                         const lf_params* params, lf_mesh* out) {
+  if (!out || !V || !F) return fail(nullptr, LF_ERR_INVALID, "null argument");
+  if (n_v < 3 || n_v >= kMaxCap) return fail(nullptr, LF_ERR_INVALID, "n_v out of range");
+  if (n_f < 1) return fail(nullptr, LF_ERR_INVALID, "n_f must be >= 1");
+  lf_params prm;
+  lf_default_params(&prm);
+  if (params) prm = *params;
+  std::string why;
+  if (!params_ok(prm, why)) return fail(nullptr, LF_ERR_INVALID, why);
+  for (int64_t f = 0; f < n_f; ++f) {
+    const int32_t a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= n_v || b >= n_v || c >= n_v)
+      return fail(nullptr, LF_ERR_INVALID, "face " + std::to_string(f) + " has a vertex out of range");
+    if (a == b || b == c || a == c)
+      return fail(nullptr, LF_ERR_INVALID, "face " + std::to_string(f) + " repeats a vertex");
+  }
+  for (int64_t i = 0; i < 3 * n_v; ++i)
+    if (!std::isfinite(V[i])) return fail(nullptr, LF_ERR_INVALID, "non-finite vertex coordinate");
+  std::vector<int64_t> rp;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  try {
+    if (!cotan_rows(n_v, V, n_f, F, rp, col, val, why)) return fail(nullptr, LF_ERR_INVALID, why);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, LF_ERR_OOM, "host allocation");
+  }
+  return finish_create(dev, n_v, rp, col, val, prm, out);
+}
+
+lf_status lf_create_mesh_csr(const lf_device* dev, int64_t n_v, const int64_t* rowptr, const int32_t* col,
+                             const double* val, const lf_params* params, lf_mesh* out) {
+  if (!out || !rowptr || (!col && rowptr && n_v > 0 && rowptr[n_v] > 0))
+    return fail(nullptr, LF_ERR_INVALID, "null argument");
+  if (n_v < 1 || n_v >= kMaxCap) return fail(nullptr, LF_ERR_INVALID, "n_v out of range");
+  lf_params prm;
+  lf_default_params(&prm);
+  if (params) prm = *params;
+  std::string why;
+  if (!params_ok(prm, why)) return fail(nullptr, LF_ERR_INVALID, why);
+  if (rowptr[0] != 0) return fail(nullptr, LF_ERR_INVALID, "rowptr[0] must be 0");
+  std::vector<int64_t> rp(static_cast<size_t>(n_v) + 1, 0);
+  std::vector<int32_t> c2;
+  std::vector<double> v2;
+  try {
+    for (int64_t i = 0; i < n_v; ++i) {
+      if (rowptr[i + 1] < rowptr[i]) return fail(nullptr, LF_ERR_INVALID, "rowptr is not monotone");
+      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        if (col[q] < 0 || col[q] >= n_v) return fail(nullptr, LF_ERR_INVALID, "column out of range");
+        if (!std::isfinite(val[q])) return fail(nullptr, LF_ERR_INVALID, "non-finite operator value");
+        if (col[q] == i) continue;                 // the diagonal is implicit
+        c2.push_back(col[q]);
+        v2.push_back(val[q]);
+      }
+      rp[static_cast<size_t>(i) + 1] = static_cast<int64_t>(c2.size());
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, LF_ERR_OOM, "host allocation");
+  }
+  return finish_create(dev, n_v, rp, c2, v2, prm, out);
+}
+
+lf_status lf_seed(lf_mesh m, const int32_t* seeds, int32_t k) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (!seeds || k < 1) return fail(m, LF_ERR_INVALID, "need k >= 1 seeds");
+  if (static_cast<int64_t>(k) + 1 > 65536) return fail(m, LF_ERR_INVALID, "k + 1 must be <= 65536");
+  if (k > m->n_v) return fail(m, LF_ERR_INVALID, "more seeds than vertices");
+  std::vector<char> used(static_cast<size_t>(m->n_v), 0);
+  for (int32_t i = 0; i < k; ++i) {
+    if (seeds[i] < 0 || seeds[i] >= m->n_v) return fail(m, LF_ERR_INVALID, "seed vertex out of range");
+    if (used[static_cast<size_t>(seeds[i])]) return fail(m, LF_ERR_INVALID, "repeated seed vertex");
+    used[static_cast<size_t>(seeds[i])] = 1;
+  }
+  auto* d_seeds = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * static_cast<size_t>(k)));
+  if (!d_seeds) return fail(m, LF_ERR_OOM, "seed upload buffer");
+  m->n_layers = k + 1;
+  m->h_job.n_layers = k + 1;
+  std::memset(&m->h_st, 0, sizeof(m->h_st));
+  LF_CUDA(m, cudaMemcpyAsync(d_seeds, seeds, sizeof(int32_t) * k, cudaMemcpyHostToDevice, m->stream));
+  LF_CUDA(m, cudaMemsetAsync(m->d_st, 0, sizeof(lf::DevStatus), m->stream));
+  LF_CUDA(m, cudaMemsetAsync(m->d_tiles, 0, sizeof(unsigned long long) * m->num_tiles, m->stream));
+  s = upload_job(m);
+  if (s != LF_OK) return s;
+  LF_CUDA(m, lf::launch_seed(m->d_job, static_cast<int>(m->n_v), k, d_seeds, m->dtype, m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  m->dfree(d_seeds);
+  m->steps = 0;
+  m->retries = 0;
+  return LF_OK;
+}
+
+lf_status lf_step(lf_mesh m, int32_t n_iters) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (n_iters < 0) return fail(m, LF_ERR_INVALID, "n_iters must be >= 0");
+  if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed or lf_set_field must come first");
+  const int64_t target = m->steps + n_iters;
+  while (m->steps < target) {
+    const int64_t todo = std::min<int64_t>(target - m->steps, kPollSteps);
+    int64_t launched = 0;
+    if (todo >= kGraphSteps) {
+      s = build_graph(m);
+      if (s != LF_OK) return s;
+      while (todo - launched >= kGraphSteps) {
+        LF_CUDA(m, cudaGraphLaunch(m->gexec, m->stream));
+        launched += kGraphSteps;
+      }
+    }
+    for (; launched < todo; ++launched)
+      LF_CUDA(m, lf::launch_step(m->d_job, m->num_tiles, m->dtype, m->tier, m->stream));
+    s = read_status(m);
+    if (s != LF_OK) return s;
+    m->steps = static_cast<int64_t>(m->h_st.epoch);
+    if (m->h_st.err == 0u) continue;
+
+    // a step failed: the field is intact in buf[epoch & 1]; fix and re-run
+    const uint32_t err = m->h_st.err;
+    if (err & lf::ERR_TIMEOUT) {
+      m->poisoned = true;
+      return fail(m, LF_ERR_TIMEOUT, "decoupled look-back wait timed out");
+    }
+    if (err & lf::ERR_ZERO_SUM) {
+      reset_after_failure(m);
+      return fail(m, LF_ERR_STATE, "a vertex summed to zero before normalisation");
+    }
+    if (err & lf::ERR_MAP) {
+      if (m->tier + 1 >= lf::kNumTiers) {
+        reset_after_failure(m);
+        return fail(m, LF_ERR_CAPACITY, "a vertex neighbourhood holds more than 160 layers");
+      }
+      ++m->tier;
+      s = ensure_tiles(m);
+      if (s == LF_OK) s = upload_job(m);
+      if (s != LF_OK) return s;
+    }
+    if (err & lf::ERR_CAPACITY) {
+      const int64_t need = static_cast<int64_t>(m->h_st.need_nnz);
+      const int64_t grown = std::max<int64_t>(need + need / 4, m->cap + m->cap / 5 + 1);
+      s = grow_capacity(m, grown);
+      if (s != LF_OK) {
+        reset_after_failure(m);
+        return s;
+      }
+    }
+    s = reset_after_failure(m);
+    if (s != LF_OK) return s;
+    ++m->retries;
+  }
+  return LF_OK;
+}
+
+lf_status lf_labels(lf_mesh m, int32_t* labels, float* maxval) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (!labels) return fail(m, LF_ERR_INVALID, "labels must not be NULL");
+  if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed or lf_set_field must come first");
+  if (!m->d_labels) {
+    m->d_labels = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * m->n_v));
+    if (!m->d_labels) return fail(m, LF_ERR_OOM, "label buffer");
+  }
+  if (maxval && m->scratch_f_len < m->n_v) {
+    m->dfree(m->d_scratch_f);
+    m->d_scratch_f = static_cast<float*>(m->dalloc(sizeof(float) * m->n_v));
+    if (!m->d_scratch_f) { m->scratch_f_len = 0; return fail(m, LF_ERR_OOM, "value buffer"); }
+    m->scratch_f_len = m->n_v;
+  }
+  LF_CUDA(m, lf::launch_labels(m->d_job, static_cast<int>(m->n_v), m->dtype, m->d_labels,
+                               maxval ? m->d_scratch_f : nullptr, m->stream));
+  LF_CUDA(m, cudaMemcpyAsync(labels, m->d_labels, sizeof(int32_t) * m->n_v, cudaMemcpyDeviceToHost, m->stream));
+  if (maxval)
+    LF_CUDA(m, cudaMemcpyAsync(maxval, m->d_scratch_f, sizeof(float) * m->n_v, cudaMemcpyDeviceToHost, m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  return LF_OK;
+}
+
+lf_status lf_get_field(lf_mesh m, int64_t* rowptr, int32_t* layer, float* val, int64_t cap, int64_t* nnz) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (!nnz) return fail(m, LF_ERR_INVALID, "nnz must not be NULL");
+  if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed or lf_set_field must come first");
+  const int cur = static_cast<int>(m->h_st.epoch & 1u);
+  std::vector<int32_t> rp(static_cast<size_t>(m->n_v) + 1);
+  LF_CUDA(m, cudaMemcpyAsync(rp.data(), m->buf[cur].rowptr, sizeof(int32_t) * (m->n_v + 1), cudaMemcpyDeviceToHost,
+                             m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  const int64_t total = rp[static_cast<size_t>(m->n_v)];
+  *nnz = total;
+  if (rowptr)
+    for (int64_t i = 0; i <= m->n_v; ++i) rowptr[i] = rp[static_cast<size_t>(i)];
+  if (!layer || !val || cap < total) return LF_OK;
+  if (total == 0) return LF_OK;
+  std::vector<uint16_t> ids(static_cast<size_t>(total));
+  LF_CUDA(m, cudaMemcpyAsync(ids.data(), m->buf[cur].ids, sizeof(uint16_t) * total, cudaMemcpyDeviceToHost,
+                             m->stream));
+  if (m->dtype == LF_F32) {
+    LF_CUDA(m, cudaMemcpyAsync(val, m->buf[cur].vals, sizeof(float) * total, cudaMemcpyDeviceToHost, m->stream));
+  } else {
+    if (m->scratch_f_len < total) {
+      m->dfree(m->d_scratch_f);
+      m->d_scratch_f = static_cast<float*>(m->dalloc(sizeof(float) * total));
+      if (!m->d_scratch_f) { m->scratch_f_len = 0; return fail(m, LF_ERR_OOM, "value buffer"); }
+      m->scratch_f_len = total;
+    }
+    LF_CUDA(m, lf::launch_widen(m->buf[cur].vals, m->d_scratch_f, total, m->dtype, m->stream));
+    LF_CUDA(m, cudaMemcpyAsync(val, m->d_scratch_f, sizeof(float) * total, cudaMemcpyDeviceToHost, m->stream));
+  }
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  for (int64_t p = 0; p < total; ++p) layer[p] = ids[static_cast<size_t>(p)];
+  return LF_OK;
+}
+
+lf_status lf_set_field(lf_mesh m, const int64_t* rowptr, const int32_t* layer, const float* val, int64_t nnz,
+                       int32_t n_layers) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (!rowptr || (nnz > 0 && (!layer || !val))) return fail(m, LF_ERR_INVALID, "null argument");
+  if (n_layers < 2 || n_layers > 65536) return fail(m, LF_ERR_INVALID, "n_layers must be in [2, 65536]");
+  if (rowptr[0] != 0 || rowptr[m->n_v] != nnz) return fail(m, LF_ERR_INVALID, "rowptr does not match nnz");
+  if (nnz >= kMaxCap) return fail(m, LF_ERR_CAPACITY, "field exceeds 2^31 entries");
+  std::vector<int32_t> rp(static_cast<size_t>(m->n_v) + 1);
+  std::vector<uint16_t> ids(static_cast<size_t>(std::max<int64_t>(nnz, 1)));
+  for (int64_t i = 0; i < m->n_v; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) return fail(m, LF_ERR_INVALID, "rowptr is not monotone");
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      if (layer[p] < 0 || layer[p] >= n_layers) return fail(m, LF_ERR_INVALID, "layer out of range");
+      if (p > rowptr[i] && layer[p] <= layer[p - 1]) return fail(m, LF_ERR_INVALID, "layers not increasing in a row");
+      if (!(val[p] > 0.0f && val[p] <= 1.0f)) return fail(m, LF_ERR_INVALID, "value not in (0, 1]");
+      ids[static_cast<size_t>(p)] = static_cast<uint16_t>(layer[p]);
+    }
+    rp[static_cast<size_t>(i)] = static_cast<int32_t>(rowptr[i]);
+  }
+  rp[static_cast<size_t>(m->n_v)] = static_cast<int32_t>(nnz);
+  if (nnz > m->cap) {
+    s = grow_capacity(m, nnz + nnz / 4 + 1);
+    if (s != LF_OK) return s;
+  }
+  const int cur = static_cast<int>(m->h_st.epoch & 1u);
+  LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].rowptr, rp.data(), sizeof(int32_t) * (m->n_v + 1), cudaMemcpyHostToDevice,
+                             m->stream));
+  if (nnz > 0) {
+    LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].ids, ids.data(), sizeof(uint16_t) * nnz, cudaMemcpyHostToDevice,
+                               m->stream));
+    if (m->dtype == LF_F32) {
+      LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].vals, val, sizeof(float) * nnz, cudaMemcpyHostToDevice, m->stream));
+    } else {
+      if (m->scratch_f_len < nnz) {
+        m->dfree(m->d_scratch_f);
+        m->d_scratch_f = static_cast<float*>(m->dalloc(sizeof(float) * nnz));
+        if (!m->d_scratch_f) { m->scratch_f_len = 0; return fail(m, LF_ERR_OOM, "value buffer"); }
+        m->scratch_f_len = nnz;
+      }
+      LF_CUDA(m, cudaMemcpyAsync(m->d_scratch_f, val, sizeof(float) * nnz, cudaMemcpyHostToDevice, m->stream));
+      LF_CUDA(m, lf::launch_narrow(m->d_scratch_f, m->buf[cur].vals, nnz, m->dtype, m->stream));
+    }
+  }
+  m->n_layers = n_layers;
+  m->h_job.n_layers = n_layers;
+  s = upload_job(m);
+  if (s != LF_OK) return s;
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  return LF_OK;
+}
+
+lf_status lf_stats(lf_mesh m, lf_stats_t* out) {
+  if (!m || !out) return fail(m, LF_ERR_INVALID, "null argument");
+  if (!m->poisoned) {
+    lf_status s = read_status(m);
+    if (s != LF_OK) return s;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->n_v = m->n_v;
+  out->n_layers = m->n_layers;
+  out->steps = m->steps;
+  out->capacity = m->cap;
+  out->operator_nnz = m->L_nnz;
+  out->skeleton_total = m->h_st.skeleton_total;
+  out->nnz_io_total = m->h_st.nnz_io_total;
+  out->device_bytes = m->device_bytes;
+  out->retries = m->retries;
+  out->map_slots = lf::kTiers[m->tier].map_slots;
+  out->field_dtype = m->dtype;
+  out->value_bytes = lf::value_bytes(m->dtype);
+  if (m->n_layers > 0 && !m->poisoned) {
+    int32_t nnz = 0;
+    const int cur = static_cast<int>(m->h_st.epoch & 1u);
+    LF_CUDA(m, cudaMemcpyAsync(&nnz, m->buf[cur].rowptr + m->n_v, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               m->stream));
+    LF_CUDA(m, cudaStreamSynchronize(m->stream));
+    out->nnz = nnz;
+  }
+  return LF_OK;
+}
+
+void lf_destroy_mesh(lf_mesh m) { delete m; }
+
+const char* lf_status_string(lf_status s) {
+  switch (s) {
+    case LF_OK: return "LF_OK";
+    case LF_ERR_INVALID: return "LF_ERR_INVALID";
+    case LF_ERR_OOM: return "LF_ERR_OOM";
+    case LF_ERR_CUDA: return "LF_ERR_CUDA";
+    case LF_ERR_TIMEOUT: return "LF_ERR_TIMEOUT";
+    case LF_ERR_STATE: return "LF_ERR_STATE";
+    case LF_ERR_CAPACITY: return "LF_ERR_CAPACITY";
+  }
+  return "LF_ERR_UNKNOWN";
+}
+
+const char* lf_last_error(lf_mesh m) { return m ? m->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point
+declared in include/lf.h, and rejects invalid arguments before any CUDA call."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1804_09152_gb300 import native
+    native.build()
+    from paper_1804_09152_gb300 import _lib
+    return _lib
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(lf_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_step", "lf_labels", "lf_get_field",
+              "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
+              "lf_default_params"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    so = ctypes.CDLL(lib.LIB)
+    for n in names:
+        assert hasattr(so, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(lf_\w+)", out))
+    assert set(names) <= exported
+    assert set(lib.EXPORTED) <= exported
+
+
+def test_default_params(lib):
+    p = lib.lf_default_params()
+    assert (p.dt, p.mu, p.w_cc, p.w_cb, p.a_cc, p.a_cb) == (5.0, 1.0, 0.2, 0.0, 0.04, 0.04)
+    assert (p.e_cc, p.e_cb, p.e_bc, p.iso, p.field_dtype, p.initial_capacity) == (0.0, 0.5, -0.5, 0.25, 0, 0)
+
+
+def test_default_params_match_oracle(lib):
+    import oracle
+    p = lib.lf_default_params()
+    for k, v in oracle.DEFAULT_PARAMS.items():
+        assert getattr(p, k) == v, k
+
+
+def test_status_strings(lib):
+    assert lib.lf_status_string(0) == "LF_OK"
+    assert lib.lf_status_string(6) == "LF_ERR_CAPACITY"
+
+
+@pytest.mark.parametrize("case", ["few_vertices", "face_range", "face_repeat", "zero_area", "bad_dt",
+                                  "bad_dtype", "nonfinite"])
+def test_create_rejects_invalid_input_without_gpu(lib, case):
+    m = synth.planar_grid(4)
+    V, F = m.V.copy(), m.F.copy()
+    params = None
+    if case == "few_vertices":
+        V, F = V[:2], F[:0]
+    elif case == "face_range":
+        F[3, 1] = 99
+    elif case == "face_repeat":
+        F[2, 2] = F[2, 0]
+    elif case == "zero_area":
+        V[F[0, 1]] = V[F[0, 0]]
+    elif case == "bad_dt":
+        params = lib.lf_default_params(dt=0.0)
+    elif case == "bad_dtype":
+        params = lib.lf_default_params(field_dtype=7)
+    elif case == "nonfinite":
+        V[5, 0] = np.nan
+    with pytest.raises(lib.LFError) as ei:
+        lib.lf_create_mesh(V, F, params=params)
+    assert ei.value.status == lib.LF_ERR_INVALID
+    assert lib.lf_last_error(None)
+
+
+def test_csr_create_rejects_invalid_input_without_gpu(lib):
+    rp = np.array([0, 2, 1, 3], np.int64)           # not monotone
+    with pytest.raises(lib.LFError):
+        lib.lf_create_mesh_csr(rp, np.array([1, 2, 0], np.int32), np.ones(3))
+    rp = np.array([0, 1, 2, 3], np.int64)
+    with pytest.raises(lib.LFError):
+        lib.lf_create_mesh_csr(rp, np.array([1, 5, 0], np.int32), np.ones(3))
+
+
+def test_package_fails_loudly_without_library(tmp_path):
+    code = ("import paper_1804_09152_gb300.native as b; b.LIB = '/nonexistent/liblf.so'\n"
+            "try:\n    import paper_1804_09152_gb300._lib\nexcept ImportError as e:\n    print('RAISED', e)\n")
+    out = subprocess.run(["python", "-c", code], capture_output=True, text=True, cwd=ROOT)
+    assert "RAISED" in out.stdout

@@ -1,0 +1,345 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 oracle.
+
+Single-step parity feeds the GPU and the oracle the same state (an oracle
+trajectory rounded to the FP32 storage of the GPU) and compares the next state
+element by element: field error <= 1e-5, identical patterns, identical
+skeleton sizes, on every row whose decisions are not within rounding of a
+flip (see parity_util).  Trajectory parity runs both from the same seeds.
+"""
+import numpy as np
+import pytest
+
+import synth
+from parity_util import FIELD_TOL, ambiguous_rows, compare, field_from_lib, to_f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lf():
+    import paper_1804_09152_gb300 as pkg
+    pkg.build()
+    from paper_1804_09152_gb300 import _lib
+    return _lib
+
+
+MESHES = {
+    # name: (mesh factory, seeds, seed stream); sizes leave a ragged last tile
+    "ico3": (lambda: synth.icosphere(3), 16, 1),
+    "grid61": (lambda: synth.planar_grid(61, seed=2), 64, 3),
+    "torus50": (lambda: synth.noisy_torus(50), 48, 5),
+}
+
+
+def single_step_parity(lf, oracle, m, seeds, checks, params=None):
+    params = params or {}
+    L = oracle.cotan_laplacian(m.V, m.F)
+    F = oracle.seed(m.n_v, seeds)
+    mesh = lf.Mesh(m.V, m.F, **params)
+    out = []
+    last = max(checks)
+    for t in range(last + 1):
+        if t in checks:
+            F32 = to_f32(F, oracle)
+            Fo, sko, mg = oracle.step(L, F32, params, margins=True)
+            mesh.set_field(F32.rowptr, F32.ids, F32.vals, F32.n_layers)
+            sk0 = mesh.stats()["skeleton_total"]
+            mesh.step(1)
+            skg = mesh.stats()["skeleton_total"] - sk0
+            Fg = field_from_lib(*mesh.get_field(), F.n_layers, oracle)
+            amb = ambiguous_rows(mg)
+            r = compare(Fo, Fg, amb)
+            r.update(t=t, sk_diff=abs(int(skg) - int(sko)))
+            out.append(r)
+        if t < last:
+            F, _ = oracle.step(L, F, params)
+    mesh.close()
+    return out
+
+
+def check_results(res, max_tie_frac=0.01):
+    for r in res:
+        assert r["max_err"] <= FIELD_TOL, r
+        assert r["pattern_mismatch"] == 0, r
+        assert r["tie_rows"] <= max_tie_frac * r["rows"], r
+        assert r["sk_diff"] <= 2 * r["tie_rows"], r
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_single_step_parity(lf, oracle_mod, name):
+    fac, k, sid = MESHES[name]
+    m = fac()
+    checks = set(range(0, 40)) | set(range(40, 160, 7))
+    res = single_step_parity(lf, oracle_mod, m, synth.sample_seeds(m.n_v, k, sid), checks)
+    check_results(res)
+
+
+@pytest.mark.parametrize("params", [
+    dict(w_cc=0.2, w_cb=0.2, a_cc=1.0, a_cb=1.0, e_cc=0.2, e_cb=0.2, e_bc=0.2),   # uniform symmetric
+    dict(dt=1.0, mu=0.7, w_cc=0.35, w_cb=0.02, a_cc=0.07, a_cb=0.05, e_cc=0.3, e_cb=0.8, e_bc=-0.1),
+])
+def test_single_step_parity_other_coefficients(lf, oracle_mod, params):
+    m = synth.planar_grid(40, seed=8)
+    res = single_step_parity(lf, oracle_mod, m, synth.sample_seeds(m.n_v, 30, 4), set(range(0, 60, 3)), params)
+    check_results(res, max_tie_frac=0.02)
+
+
+def test_trajectory_icosphere_300_steps(lf, oracle_mod):
+    """Icosphere level 3, 16 seeds, 300 steps from the same seeds.
+
+    Ties between two cells are unstable (the w_cc term doubles a deviation
+    every step), so a rounding difference at a tied vertex picks a side.  The
+    tied set is found from the oracle alone: a second oracle run that rounds
+    its state to FP32 after every step; vertices (and their 1-ring) where the
+    two oracle runs differ are excluded, the rest must match the GPU.
+    """
+    m = synth.icosphere(3)
+    seeds = synth.sample_seeds(m.n_v, 16, 1)
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    F = oracle_mod.seed(m.n_v, seeds)
+    Fr = F
+    for _ in range(300):
+        F, _ = oracle_mod.step(L, F)
+        Fr, _ = oracle_mod.step(L, to_f32(Fr, oracle_mod))
+    mesh = lf.Mesh(m.V, m.F)
+    mesh.seed(seeds)
+    mesh.step(300)
+    lab_g = mesh.labels()
+    Fg = field_from_lib(*mesh.get_field(), F.n_layers, oracle_mod)
+    lab_o = oracle_mod.labels(F)
+    D, Dr, Dg = F.dense(), Fr.dense(), Fg.dense()
+    sens = (np.abs(D - Dr).max(axis=1) > FIELD_TOL) | (lab_o != oracle_mod.labels(Fr))
+    A = np.abs(L.dense()) > 0
+    sens = (A.astype(int) @ sens.astype(int)) > 0
+    stable = ~sens
+    assert stable.mean() > 0.8, stable.mean()
+    assert np.array_equal(lab_g[stable], lab_o[stable])
+    assert np.abs(Dg - D)[stable].max() <= FIELD_TOL
+    assert np.mean(lab_g == lab_o) > 0.95
+
+
+def test_full_size_grid512(lf, oracle_mod):
+    """512 x 512 jittered grid, 1024 seeds: the size the benchmark times."""
+    import scipy.sparse as sp
+    m = synth.planar_grid(512, jitter=0.2, seed=2)
+    seeds = synth.sample_seeds(m.n_v, 1024, 3)
+    res = single_step_parity(lf, oracle_mod, m, seeds, {0, 1, 4, 12, 30})
+    check_results(res)
+    # 2000 steps in the benchmark's launch configuration, then properties that
+    # hold at any size
+    mesh = lf.Mesh(m.V, m.F)
+    mesh.seed(seeds)
+    mesh.step(1999)
+    rp0, lay0, val0 = mesh.get_field()
+    mesh.step(1)
+    rp1, lay1, val1 = mesh.get_field()
+    lab = mesh.labels()
+    rows = np.repeat(np.arange(m.n_v), np.diff(rp1))
+    rs = np.bincount(rows, weights=val1.astype(np.float64), minlength=m.n_v)
+    assert np.abs(rs - 1.0).max() < 1e-5
+    assert val1.min() > 0 and val1.max() <= 1.0
+    same_row = rows[1:] == rows[:-1]
+    assert np.all(lay1[1:][same_row] > lay1[:-1][same_row])
+    assert set(lab.tolist()) == set(range(1024))
+    Lo = oracle_mod.cotan_laplacian(m.V, m.F)
+    A = sp.csr_matrix((np.ones(Lo.col.size), Lo.col, Lo.rowptr), shape=(m.n_v, m.n_v))
+    P0 = sp.csr_matrix((np.ones(lay0.size), lay0, rp0), shape=(m.n_v, 1025))
+    P1 = sp.csr_matrix((np.ones(lay1.size), lay1, rp1), shape=(m.n_v, 1025))
+    reach = (A @ P0) > 0
+    assert (P1 > reach).nnz == 0          # no layer moved more than one ring
+    st = mesh.stats()
+    assert st["steps"] == 2000 and st["skeleton_total"] > 0
+
+
+def test_capacity_growth_rerun_is_bit_exact(lf):
+    m = synth.icosphere(3)
+    seeds = synth.sample_seeds(m.n_v, 16, 1)
+    a = lf.Mesh(m.V, m.F)
+    a.seed(seeds)
+    a.step(120)
+    b = lf.Mesh(m.V, m.F, initial_capacity=m.n_v)
+    b.seed(seeds)
+    b.step(120)
+    sa, sb = a.stats(), b.stats()
+    assert sa["retries"] == 0 and sb["retries"] > 0 and sb["capacity"] > m.n_v
+    for x, y in zip(a.get_field(), b.get_field()):
+        assert np.array_equal(x, y)
+    assert sa["skeleton_total"] == sb["skeleton_total"]
+
+
+def random_field(n_v, n_layers, per_row, rng):
+    rp = [0]
+    ids, vals = [], []
+    for i in range(n_v):
+        r = int(rng.integers(1, per_row + 1))
+        ls = np.sort(rng.choice(n_layers, size=r, replace=False))
+        v = rng.random(r) + 0.05
+        v /= v.sum()
+        ids.extend(ls.tolist())
+        vals.extend(v.tolist())
+        rp.append(len(ids))
+    return np.array(rp, np.int64), np.array(ids, np.int32), np.array(vals, np.float32)
+
+
+def test_map_tiers_escalate_and_match(lf, oracle_mod):
+    m = synth.planar_grid(20, seed=6)
+    rng = np.random.default_rng(5)
+    for per_row, n_layers, want_slots in [(5, 200, 48), (14, 400, 160)]:
+        rp, ids, vals = random_field(m.n_v, n_layers, per_row, rng)
+        mesh = lf.Mesh(m.V, m.F)
+        mesh.set_field(rp, ids, vals, n_layers)
+        mesh.step(1)
+        st = mesh.stats()
+        assert st["map_slots"] == want_slots and st["retries"] >= 1
+        L = oracle_mod.cotan_laplacian(m.V, m.F)
+        Fin = oracle_mod.Field(rp, ids, vals.astype(np.float64), n_layers)
+        Fo, _, mg = oracle_mod.step(L, Fin, margins=True)
+        Fg = field_from_lib(*mesh.get_field(), n_layers, oracle_mod)
+        r = compare(Fo, Fg, ambiguous_rows(mg))
+        assert r["max_err"] <= FIELD_TOL and r["pattern_mismatch"] == 0, r
+        mesh.close()
+
+
+def test_map_overflow_beyond_last_tier_is_an_error(lf):
+    m = synth.planar_grid(12, seed=6)
+    rp, ids, vals = random_field(m.n_v, 4000, 40, np.random.default_rng(2))
+    mesh = lf.Mesh(m.V, m.F)
+    mesh.set_field(rp, ids, vals, 4000)
+    with pytest.raises(lf.LFError) as ei:
+        mesh.step(1)
+    assert ei.value.status == lf.LF_ERR_CAPACITY
+    # the handle stays usable and the field is unchanged
+    rp2, ids2, vals2 = mesh.get_field()
+    assert np.array_equal(rp2, rp) and np.array_equal(ids2, ids) and np.array_equal(vals2, vals)
+
+
+def test_checkpoint_resume_is_bit_exact(lf):
+    m = synth.noisy_torus(40)
+    seeds = synth.sample_seeds(m.n_v, 30, 7)
+    a = lf.Mesh(m.V, m.F)
+    a.seed(seeds)
+    a.step(45)
+    ck = a.get_field()
+    a.step(80)
+    b = lf.Mesh(m.V, m.F)
+    b.set_field(*ck, 31)
+    b.step(80)
+    for x, y in zip(a.get_field(), b.get_field()):
+        assert np.array_equal(x, y)
+
+
+def test_deterministic(lf):
+    m = synth.planar_grid(96, seed=9)
+    seeds = synth.sample_seeds(m.n_v, 80, 9)
+    outs = []
+    for _ in range(2):
+        x = lf.Mesh(m.V, m.F)
+        x.seed(seeds)
+        x.step(300)
+        outs.append(x.get_field())
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
+
+
+def test_torch_allocator_and_stream(lf):
+    import torch
+    m = synth.icosphere(3)
+    seeds = synth.sample_seeds(m.n_v, 16, 1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        dev = lf.torch_device()
+        a = lf.Mesh(m.V, m.F, device=dev)
+        a.seed(seeds)
+        a.step(150)
+        fa = a.get_field()
+        a.close()
+    b = lf.Mesh(m.V, m.F)
+    b.seed(seeds)
+    b.step(150)
+    for x, y in zip(fa, b.get_field()):
+        assert np.array_equal(x, y)
+
+
+def test_single_seed_and_tiny_mesh(lf, oracle_mod):
+    V = np.array([[0, 0, 0], [1, 0, 0], [0.3, 0.8, 0]], float)
+    F = np.array([[0, 1, 2]], np.int32)
+    tri = synth.Mesh(V, F)
+    res = single_step_parity(lf, oracle_mod, tri, np.array([1], np.int32), set(range(12)))
+    check_results(res, max_tie_frac=1.0)
+    m = synth.icosphere(2)
+    res = single_step_parity(lf, oracle_mod, m, np.array([17], np.int32), set(range(0, 30)))
+    check_results(res)
+
+
+def test_maximum_layer_count(lf, oracle_mod):
+    m = synth.planar_grid(256, seed=12)                 # 65536 vertices
+    seeds = synth.sample_seeds(m.n_v, 65535, 13)        # k + 1 = 65536 layers
+    res = single_step_parity(lf, oracle_mod, m, seeds, {0, 1, 2, 3})
+    check_results(res)
+    mesh = lf.Mesh(m.V, m.F)
+    with pytest.raises(lf.LFError):
+        big = synth.planar_grid(257, seed=12)
+        lf.Mesh(big.V, big.F).seed(np.arange(65536, dtype=np.int32))
+
+
+def test_csr_entry_matches_mesh_entry(lf, oracle_mod):
+    m = synth.noisy_torus(30)
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    seeds = synth.sample_seeds(m.n_v, 20, 3)
+    a = lf.Mesh(csr=(L.rowptr, L.col, L.val))
+    b = lf.Mesh(m.V, m.F)
+    for x in (a, b):
+        x.seed(seeds)
+        x.step(1)
+    Fa = field_from_lib(*a.get_field(), 21, oracle_mod)
+    Fb = field_from_lib(*b.get_field(), 21, oracle_mod)
+    assert compare(Fa, Fb)["max_err_all"] <= FIELD_TOL
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_reduced_precision_storage(lf, oracle_mod, dtype):
+    """Field values stored in 16 bits, FP32 arithmetic: errors are reported, not gated
+    at FP32 level; labels must still agree with the FP64 oracle on most vertices."""
+    m = synth.icosphere(3)
+    seeds = synth.sample_seeds(m.n_v, 16, 1)
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    F, _ = oracle_mod.run(L, oracle_mod.seed(m.n_v, seeds), 300)
+    mesh = lf.Mesh(m.V, m.F, field_dtype=dtype)
+    mesh.seed(seeds)
+    mesh.step(300)
+    lab = mesh.labels()
+    Fg = field_from_lib(*mesh.get_field(), 17, oracle_mod)
+    agree = np.mean(lab == oracle_mod.labels(F))
+    err = compare(F, Fg)["max_err_all"]
+    print(f"{dtype}: label agreement {agree:.4f}, max field error {err:.3e}")
+    assert agree > 0.9 and np.isfinite(err)
+    assert mesh.stats()["value_bytes"] == 2
+
+
+def test_invalid_calls(lf):
+    m = synth.icosphere(1)
+    mesh = lf.Mesh(m.V, m.F)
+    with pytest.raises(lf.LFError) as ei:
+        mesh.step(1)
+    assert ei.value.status == lf.LF_ERR_STATE
+    with pytest.raises(lf.LFError) as ei:
+        mesh.labels()
+    assert ei.value.status == lf.LF_ERR_STATE
+    for bad in ([0, 0], [m.n_v], [-1]):
+        with pytest.raises(lf.LFError) as ei:
+            mesh.seed(np.array(bad, np.int32))
+        assert ei.value.status == lf.LF_ERR_INVALID
+    mesh.seed(np.array([0, 5], np.int32))
+    with pytest.raises(lf.LFError) as ei:
+        mesh.step(-1)
+    assert ei.value.status == lf.LF_ERR_INVALID
+    f0 = mesh.get_field()
+    mesh.step(0)
+    assert mesh.stats()["steps"] == 0
+    for x, y in zip(f0, mesh.get_field()):
+        assert np.array_equal(x, y)
+    rp, ids, vals = f0
+    with pytest.raises(lf.LFError):
+        mesh.set_field(rp, ids, vals * 2.0, 3)         # values above 1
+    with pytest.raises(lf.LFError):
+        mesh.set_field(rp, ids, vals, 1)               # too few layers
