@@ -208,8 +208,8 @@ def step(L, F, params=None, W=None, A=None, E=None, margins=False):
     """One time-iteration of Algorithm 1 (literal triple loop).
 
     Returns ``(F_next, skeleton)`` or ``(F_next, skeleton, margins)`` where
-    ``margins`` is (n_v, 3): min |G| over entering candidates, min |F + d dt|
-    over the skeleton, and n_i.
+    ``margins`` is (n_v, 3): the relative distance of the irows test and of
+    the clamp to zero from flipping (see lf_oracle.c), and n_i.
     """
     lib = _load()
     co = _coefs(params)

@@ -205,11 +205,12 @@ static void sort_ids(int32_t* a, int32_t n) {
 static int64_t lt_product(int64_t n_v, int32_t n_layers,
                           const int64_t* Lrp, const int32_t* Lcol, const double* Lval,
                           const int64_t* Frp, const int32_t* Fid, const double* Fval,
-                          int64_t cap, int64_t* Grp, int32_t* Gid, double* Gval) {
+                          int64_t cap, int64_t* Grp, int32_t* Gid, double* Gval, double* Gabs) {
   double* acc = (double*)calloc((size_t)n_layers, sizeof(double));
+  double* aab = (double*)calloc((size_t)n_layers, sizeof(double));
   char* mark = (char*)calloc((size_t)n_layers, 1);
   int32_t* touched = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_layers);
-  if (!acc || !mark || !touched) { free(acc); free(mark); free(touched); return ORC_ERR_NOMEM; }
+  if (!acc || !aab || !mark || !touched) { free(acc); free(aab); free(mark); free(touched); return ORC_ERR_NOMEM; }
   int64_t o = 0;
   Grp[0] = 0;
   for (int64_t i = 0; i < n_v; ++i) {
@@ -219,19 +220,24 @@ static int64_t lt_product(int64_t n_v, int32_t n_layers,
       double lij = Lval[q];
       for (int64_t p = Frp[j]; p < Frp[j + 1]; ++p) {
         int32_t l = Fid[p];
-        if (!mark[l]) { mark[l] = 1; touched[nt++] = l; acc[l] = 0.0; }
+        if (!mark[l]) { mark[l] = 1; touched[nt++] = l; acc[l] = 0.0; aab[l] = 0.0; }
         acc[l] += lij * Fval[p];
+        aab[l] += fabs(lij * Fval[p]);
       }
     }
     sort_ids(touched, nt);
     for (int32_t x = 0; x < nt; ++x) {
-      if (o < cap) { Gid[o] = touched[x]; Gval[o] = acc[touched[x]]; }
+      if (o < cap) {
+        Gid[o] = touched[x];
+        Gval[o] = acc[touched[x]];
+        if (Gabs) Gabs[o] = aab[touched[x]];
+      }
       ++o;
       mark[touched[x]] = 0;
     }
     Grp[i + 1] = o;
   }
-  free(acc); free(mark); free(touched);
+  free(acc); free(aab); free(mark); free(touched);
   return o > cap ? -o - 16 : o;
 }
 
@@ -239,7 +245,7 @@ int64_t orc_lt(int64_t n_v, int32_t n_layers,
                const int64_t* Lrp, const int32_t* Lcol, const double* Lval,
                const int64_t* Frp, const int32_t* Fid, const double* Fval,
                int64_t cap, int64_t* Grp, int32_t* Gid, double* Gval) {
-  return lt_product(n_v, n_layers, Lrp, Lcol, Lval, Frp, Fid, Fval, cap, Grp, Gid, Gval);
+  return lt_product(n_v, n_layers, Lrp, Lcol, Lval, Frp, Fid, Fval, cap, Grp, Gid, Gval, NULL);
 }
 
 /*
@@ -263,9 +269,13 @@ int64_t orc_lt(int64_t n_v, int32_t n_layers,
  * Output arrays have capacity out_cap.  Returns the output nnz, or
  * -(needed nnz) - 16 when out_cap is too small, or a negative error code.
  * skeleton: if non-NULL receives sum_i n_i.
- * margins: if non-NULL, 3 doubles per vertex: min |G(i,l)| over the entries
- *   of G with F(i,l) = 0 (the irows decision), min |F_j + d dt| over irows
- *   (the clamp to zero), and n_i; HUGE_VAL where there is no such entry.
+ * margins: if non-NULL, 3 doubles per vertex describing how far its two
+ *   discrete decisions are from flipping under rounding:
+ *   [0] min over the entries of G with F(i,l) = 0 of |G_il| / sum_j |L_ij F_jl|
+ *       (the irows test),
+ *   [1] min over irows of |F_j + d dt| / (|F_j| + dt sum of |terms of d|)
+ *       (the clamp to zero),
+ *   [2] n_i.  HUGE_VAL where there is no such entry.
  */
 int64_t orc_step(int64_t n_v, int32_t n_layers,
                  const int64_t* Lrp, const int32_t* Lcol, const double* Lval,
@@ -279,6 +289,7 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
   int64_t gcap = 8 * (Frp[n_v] + n_v) + 16;
   int32_t* Gid = NULL;
   double* Gval = NULL;
+  double* Gab = NULL;
   int64_t* Hrp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_v + 1));
   int32_t* Hid = NULL;
   double* Hval = NULL;
@@ -291,10 +302,11 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
   for (;;) {
     Gid = (int32_t*)malloc(sizeof(int32_t) * (size_t)gcap);
     Gval = (double*)malloc(sizeof(double) * (size_t)gcap);
-    if (!Gid || !Gval) { ret = ORC_ERR_NOMEM; goto done; }
-    int64_t g = lt_product(n_v, n_layers, Lrp, Lcol, Lval, Frp, Fid, Fval, gcap, Grp, Gid, Gval);
+    Gab = (double*)malloc(sizeof(double) * (size_t)gcap);
+    if (!Gid || !Gval || !Gab) { ret = ORC_ERR_NOMEM; goto done; }
+    int64_t g = lt_product(n_v, n_layers, Lrp, Lcol, Lval, Frp, Fid, Fval, gcap, Grp, Gid, Gval, Gab);
     if (g >= 0) break;
-    free(Gid); free(Gval); Gid = NULL; Gval = NULL;
+    free(Gid); free(Gval); free(Gab); Gid = NULL; Gval = NULL; Gab = NULL;
     if (g > -16) { ret = g; goto done; }
     gcap = -(g + 16);
   }
@@ -317,9 +329,10 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
       int32_t l = lf < lg ? lf : lg;
       double fv = (lf == l) ? Fval[pf] : 0.0;
       double gv = (lg == l) ? Gval[pg] : 0.0;
+      double ga = (lg == l) ? Gab[pg] : 0.0;
       if (lf == l) ++pf;
       if (lg == l) ++pg;
-      if (fv == 0.0 && fabs(gv) < mG) mG = fabs(gv);
+      if (fv == 0.0 && ga > 0.0 && fabs(gv) / ga < mG) mG = fabs(gv) / ga;
       if (fv > 0.0 || (fv == 0.0 && gv > 0.0)) {
         S[n] = l; SF[n] = fv; SG[n] = gv; ++n;
       }
@@ -328,19 +341,24 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
     Hrp[i + 1] = Hrp[i] + n;
     for (int32_t jj = 0; jj < n; ++jj) {
       int32_t j = S[jj];
-      double d = 0.0;
+      double d = 0.0, dabs = 0.0;
       for (int32_t kk = 0; kk < n; ++kk) {
         int32_t kx = S[kk];
-        double sum = 0.0;
+        double sum = 0.0, sabs = 0.0;
         for (int32_t ll = 0; ll < n; ++ll) {
           int32_t l = S[ll];
-          sum += 0.5 * (coef_sym(Am, c.a_cc, c.a_cb, n_layers, j, l) - coef_sym(Am, c.a_cc, c.a_cb, n_layers, kx, l)) * SG[ll]
-               + (coef_sym(Wm, c.w_cc, c.w_cb, n_layers, j, l) - coef_sym(Wm, c.w_cc, c.w_cb, n_layers, kx, l)) * SF[ll];
+          double ta = 0.5 * (coef_sym(Am, c.a_cc, c.a_cb, n_layers, j, l) - coef_sym(Am, c.a_cc, c.a_cb, n_layers, kx, l)) * SG[ll];
+          double tw = (coef_sym(Wm, c.w_cc, c.w_cb, n_layers, j, l) - coef_sym(Wm, c.w_cc, c.w_cb, n_layers, kx, l)) * SF[ll];
+          sum += ta + tw;
+          sabs += fabs(ta) + fabs(tw);
         }
-        d += -(c.mu / n) * (sum - coef_e(Em, &c, n_layers, j, kx) * sqrt(SF[jj] * SF[kk]));
+        double te = coef_e(Em, &c, n_layers, j, kx) * sqrt(SF[jj] * SF[kk]);
+        d += -(c.mu / n) * (sum - te);
+        dabs += (c.mu / n) * (sabs + fabs(te));
       }
       double v = SF[jj] + d * c.dt;
-      if (fabs(v) < mC) mC = fabs(v);
+      double vscale = fabs(SF[jj]) + c.dt * dabs;
+      if (vscale > 0.0 && fabs(v) / vscale < mC) mC = fabs(v) / vscale;
       if (v > 1.0) v = 1.0;
       if (v <= 0.0) v = 0.0;
       Hid[Hrp[i] + jj] = j;
@@ -379,7 +397,7 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
   }
 
 done:
-  free(Grp); free(Gid); free(Gval); free(Hrp); free(Hid); free(Hval);
+  free(Grp); free(Gid); free(Gval); free(Gab); free(Hrp); free(Hid); free(Hval);
   free(S); free(SF); free(SG);
   return ret;
 }
