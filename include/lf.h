@@ -106,7 +106,8 @@ typedef struct {
   uint64_t nnz_io_total;  /* sum over completed steps of nnz(in) + nnz(out)     */
   int64_t device_bytes;   /* device memory held by the handle                  */
   int32_t retries;        /* steps re-run after a capacity or map overflow     */
-  int32_t map_slots;      /* per-vertex layer-union slots of the step kernel   */
+  int32_t map_slots;      /* register slots of the step kernel's fast path;
+                             larger layer unions take its exact slow path     */
   int32_t field_dtype;    /* lf_dtype                                          */
   int32_t value_bytes;    /* bytes per stored field value                      */
 } lf_stats_t;
@@ -159,12 +160,12 @@ lf_status lf_seed(lf_mesh m, const int32_t* seed_vertices, int32_t k);
  * update of Eq. 11-13 over the skeleton with clamping to [0, 1], the
  * normalisation of every vertex to sum 1 and the removal of zero entries
  * (Sec. 4).  Every d uses the values before the step.  Returns after the
- * work is done on the device.  When a field buffer or the per-vertex layer
- * union overflows, the library grows it (by at least 20 %, Sec. 4) and re-runs
- * the step; results do not depend on it.
+ * work is done on the device.  When the output outgrows a field buffer, the
+ * library grows it (by at least 20 %, Sec. 4) and re-runs the step; results
+ * do not depend on it.  Any number of layers per neighbourhood is handled.
  * Errors: LF_ERR_STATE before lf_seed; LF_ERR_INVALID for n_iters < 0;
  * LF_ERR_OOM when growth fails (the field stays at the last completed step);
- * LF_ERR_CAPACITY when a vertex sees more layers than the library supports;
+ * LF_ERR_CAPACITY when the field would exceed 2^31 entries;
  * LF_ERR_TIMEOUT, LF_ERR_CUDA.
  */
 lf_status lf_step(lf_mesh m, int32_t n_iters);

@@ -38,9 +38,8 @@ struct lf_mesh_s {
   int64_t L_nnz = 0;
   int dtype = 0;
   int n_layers = 0;
-  int64_t cap = 0;
   int num_tiles = 0;
-  int tier = 0;
+  int64_t tile_cap = 0;          // entries per tile segment
   int64_t steps = 0;
   int retries = 0;
   bool poisoned = false;
@@ -52,8 +51,6 @@ struct lf_mesh_s {
   int2* d_Lcv = nullptr;
   lf::FieldBuf buf[2]{};
   lf::DevStatus* d_st = nullptr;
-  unsigned long long* d_tiles = nullptr;
-  int tiles_alloc = 0;
   lf::JobDesc* d_job = nullptr;
   lf::JobDesc h_job{};
   lf::DevStatus h_st{};
@@ -62,13 +59,14 @@ struct lf_mesh_s {
   int64_t scratch_f_len = 0;
 
   cudaGraphExec_t gexec = nullptr;
-  int graph_tier = -1;
 
   ~lf_mesh_s() {
     cudaStreamSynchronize(stream);
     if (gexec) cudaGraphExecDestroy(gexec);
     for (auto& a : allocs) release(a.p);
   }
+
+  int64_t buffer_entries() const { return static_cast<int64_t>(num_tiles) * tile_cap; }
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -114,7 +112,10 @@ lf_status fail(lf_mesh m, lf_status s, const std::string& msg) {
   return s;
 }
 
+// A failed CUDA call poisons the handle.  The runtime's per-thread error slot
+// is cleared so that it does not surface in a later, unrelated call.
 lf_status cuda_fail(lf_mesh m, cudaError_t e, const char* where) {
+  cudaGetLastError();
   if (m) m->poisoned = true;
   return fail(m, LF_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
@@ -196,75 +197,55 @@ lf_status upload_job(lf_mesh m) {
   return LF_OK;
 }
 
+lf_status upload_status(lf_mesh m) {
+  LF_CUDA(m, cudaMemcpyAsync(m->d_st, &m->h_st, sizeof(lf::DevStatus), cudaMemcpyHostToDevice, m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  return LF_OK;
+}
+
 lf_status read_status(lf_mesh m) {
   LF_CUDA(m, cudaMemcpyAsync(&m->h_st, m->d_st, sizeof(lf::DevStatus), cudaMemcpyDeviceToHost, m->stream));
   LF_CUDA(m, cudaStreamSynchronize(m->stream));
   return LF_OK;
 }
 
-// Clears the error state and the scan state after a failed step.
+// Clears the error state and the per-step counters after a failed step.
 lf_status reset_after_failure(lf_mesh m) {
-  lf::DevStatus s = m->h_st;
+  lf::DevStatus& s = m->h_st;
   s.err = 0;
-  s.ticket = 0;
   s.done = 0;
-  s.need_nnz = 0;
-  s.need_map = 0;
+  s.need_tile = 0;
   s.skeleton_step = 0;
-  m->h_st = s;
-  LF_CUDA(m, cudaMemcpyAsync(m->d_st, &s, sizeof(s), cudaMemcpyHostToDevice, m->stream));
-  LF_CUDA(m, cudaMemsetAsync(m->d_tiles, 0, sizeof(unsigned long long) * m->num_tiles, m->stream));
-  return LF_OK;
+  s.nnz_io_step = 0;
+  s.nnz_step = 0;
+  return upload_status(m);
 }
 
-int tiles_for(int64_t n_v, int tier) {
-  const int b = lf::kTiers[tier].block;
-  return static_cast<int>((n_v + b - 1) / b);
-}
+int64_t round16(int64_t x) { return (x + 15) / 16 * 16; }
 
-// (Re)allocates the look-back words for the current tier.
-lf_status ensure_tiles(lf_mesh m) {
-  const int need = tiles_for(m->n_v, m->tier);
-  if (need > m->tiles_alloc) {
-    auto* p = static_cast<unsigned long long*>(m->dalloc(sizeof(unsigned long long) * need));
-    if (!p) return fail(m, LF_ERR_OOM, "allocating tile status");
-    m->dfree(m->d_tiles);
-    m->d_tiles = p;
-    m->tiles_alloc = need;
-  }
-  m->num_tiles = need;
-  m->h_job.num_tiles = need;
-  m->h_job.tile_status = m->d_tiles;
-  LF_CUDA(m, cudaMemsetAsync(m->d_tiles, 0, sizeof(unsigned long long) * need, m->stream));
-  return LF_OK;
-}
-
-// Grows both field buffers to new_cap entries, keeping the current field.
-lf_status grow_capacity(lf_mesh m, int64_t new_cap) {
-  if (new_cap > kMaxCap) return fail(m, LF_ERR_CAPACITY, "field exceeds 2^31 entries");
+// Gives every tile segment new_cap entries.  With keep, the current field is
+// moved into the new segments on the device (rows keep their order).
+lf_status set_tile_cap(lf_mesh m, int64_t new_cap, bool keep) {
+  new_cap = round16(std::max<int64_t>(new_cap, lf::kTile));
+  const int64_t entries = static_cast<int64_t>(m->num_tiles) * new_cap;
+  if (entries > kMaxCap) return fail(m, LF_ERR_CAPACITY, "field exceeds 2^31 entries");
   const int vb = lf::value_bytes(m->dtype);
   const int cur = static_cast<int>(m->h_st.epoch & 1u);
-  int32_t nnz = 0;
-  if (m->buf[cur].ids) {
-    LF_CUDA(m, cudaMemcpyAsync(&nnz, m->buf[cur].rowptr + m->n_v, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                               m->stream));
-    LF_CUDA(m, cudaStreamSynchronize(m->stream));
-  }
   void* ids[2] = {nullptr, nullptr};
   void* vals[2] = {nullptr, nullptr};
   for (int b = 0; b < 2; ++b) {
-    ids[b] = m->dalloc(sizeof(uint16_t) * static_cast<size_t>(new_cap));
-    vals[b] = m->dalloc(static_cast<size_t>(vb) * static_cast<size_t>(new_cap));
+    ids[b] = m->dalloc(sizeof(uint16_t) * static_cast<size_t>(entries));
+    vals[b] = m->dalloc(static_cast<size_t>(vb) * static_cast<size_t>(entries));
     if (!ids[b] || !vals[b]) {
       for (int c = 0; c <= b; ++c) { m->dfree(ids[c]); m->dfree(vals[c]); }
       return fail(m, LF_ERR_OOM, "growing the field buffers");
     }
   }
-  if (nnz > 0 && m->buf[cur].ids) {
-    LF_CUDA(m, cudaMemcpyAsync(ids[cur], m->buf[cur].ids, sizeof(uint16_t) * nnz, cudaMemcpyDeviceToDevice,
-                               m->stream));
-    LF_CUDA(m, cudaMemcpyAsync(vals[cur], m->buf[cur].vals, static_cast<size_t>(vb) * nnz,
-                               cudaMemcpyDeviceToDevice, m->stream));
+  if (keep && m->buf[cur].ids) {
+    LF_CUDA(m, lf::launch_relayout(m->buf[cur].rows, m->buf[cur].ids, m->buf[cur].vals,
+                                   static_cast<int>(m->tile_cap), m->buf[cur].rows,
+                                   static_cast<uint16_t*>(ids[cur]), vals[cur], static_cast<int>(new_cap),
+                                   static_cast<int>(m->n_v), m->dtype, m->stream));
   }
   LF_CUDA(m, cudaStreamSynchronize(m->stream));
   for (int b = 0; b < 2; ++b) {
@@ -274,42 +255,46 @@ lf_status grow_capacity(lf_mesh m, int64_t new_cap) {
     m->buf[b].vals = vals[b];
     m->h_job.buf[b] = m->buf[b];
   }
-  m->cap = new_cap;
-  m->h_job.cap = static_cast<int32_t>(new_cap);
+  m->tile_cap = new_cap;
+  m->h_job.tile_cap = static_cast<int32_t>(new_cap);
   return upload_job(m);
 }
 
+// A graph of kGraphSteps step launches chained by programmatic edges: each
+// launch may start its CTAs while the previous one drains, and waits inside
+// the kernel (griddepcontrol.wait) before it reads the previous step's output.
 lf_status build_graph(lf_mesh m) {
-  if (m->gexec && m->graph_tier == m->tier) return LF_OK;
-  if (m->gexec) {
-    cudaGraphExecDestroy(m->gexec);
-    m->gexec = nullptr;
-  }
-  size_t smem = 0;
-  const void* fn = lf::step_kernel(m->dtype, m->tier, &smem);
+  if (m->gexec) return LF_OK;
+  const void* fn = lf::step_kernel(m->dtype);
   cudaGraph_t g = nullptr;
   LF_CUDA(m, cudaGraphCreate(&g, 0));
   void* args[1] = {&m->d_job};
   cudaKernelNodeParams p{};
   p.func = const_cast<void*>(fn);
   p.gridDim = dim3(static_cast<unsigned>(m->num_tiles));
-  p.blockDim = dim3(static_cast<unsigned>(lf::kTiers[m->tier].block));
-  p.sharedMemBytes = static_cast<unsigned>(smem);
+  p.blockDim = dim3(static_cast<unsigned>(lf::kTile));
+  p.sharedMemBytes = 0;
   p.kernelParams = args;
   cudaGraphNode_t prev = nullptr;
   for (int s = 0; s < kGraphSteps; ++s) {
     cudaGraphNode_t node = nullptr;
-    cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+    cudaError_t e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &p);
+    if (e == cudaSuccess && prev) {
+      cudaGraphEdgeData ed{};
+      ed.from_port = cudaGraphKernelNodePortProgrammatic;
+      ed.to_port = 0;
+      ed.type = cudaGraphDependencyTypeProgrammatic;
+      e = cudaGraphAddDependencies(g, &prev, &node, &ed, 1);
+    }
     if (e != cudaSuccess) {
       cudaGraphDestroy(g);
-      return cuda_fail(m, e, "cudaGraphAddKernelNode");
+      return cuda_fail(m, e, "building the step graph");
     }
     prev = node;
   }
   cudaError_t e = cudaGraphInstantiate(&m->gexec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(m, e, "cudaGraphInstantiate");
-  m->graph_tier = m->tier;
   return LF_OK;
 }
 
@@ -323,12 +308,6 @@ lf_status check_usable(lf_mesh m) {
 lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int64_t>& rp,
                         const std::vector<int32_t>& col, const std::vector<double>& val,
                         const lf_params& prm, lf_mesh* out) {
-  static bool kernels_ready = false;
-  if (!kernels_ready) {
-    cudaError_t e = lf::init_kernels();
-    if (e != cudaSuccess) return fail(nullptr, LF_ERR_CUDA, std::string("init_kernels: ") + cudaGetErrorString(e));
-    kernels_ready = true;
-  }
   lf_mesh m = new (std::nothrow) lf_mesh_s();
   if (!m) return fail(nullptr, LF_ERR_OOM, "host allocation");
   if (dev) m->dev = *dev;
@@ -336,6 +315,7 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
   m->params = prm;
   m->n_v = n_v;
   m->dtype = prm.field_dtype;
+  m->num_tiles = static_cast<int>((n_v + lf::kTile - 1) / lf::kTile);
   const int64_t nnz = static_cast<int64_t>(col.size());
   if (nnz >= kMaxCap) {
     delete m;
@@ -355,8 +335,8 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
   m->d_Lcv = static_cast<int2*>(m->dalloc(sizeof(int2) * std::max<int64_t>(nnz, 1)));
   m->d_st = static_cast<lf::DevStatus*>(m->dalloc(sizeof(lf::DevStatus)));
   m->d_job = static_cast<lf::JobDesc*>(m->dalloc(sizeof(lf::JobDesc)));
-  for (int b = 0; b < 2; ++b) m->buf[b].rowptr = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * (n_v + 1)));
-  if (!m->d_Lrp || !m->d_Lcv || !m->d_st || !m->d_job || !m->buf[0].rowptr || !m->buf[1].rowptr) {
+  for (int b = 0; b < 2; ++b) m->buf[b].rows = static_cast<int2*>(m->dalloc(sizeof(int2) * n_v));
+  if (!m->d_Lrp || !m->d_Lcv || !m->d_st || !m->d_job || !m->buf[0].rows || !m->buf[1].rows) {
     delete m;
     return fail(nullptr, LF_ERR_OOM, "device allocation");
   }
@@ -368,12 +348,14 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_st, 0, sizeof(lf::DevStatus), m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     delete m;
     return fail(nullptr, LF_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
   }
   lf::JobDesc& j = m->h_job;
   j.n_v = static_cast<int32_t>(n_v);
   j.n_layers = 0;
+  j.num_tiles = m->num_tiles;
   j.L_rowptr = m->d_Lrp;
   j.L_colval = m->d_Lcv;
   j.buf[0] = m->buf[0];
@@ -382,9 +364,10 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
   j.c = lf::Coefs{static_cast<float>(prm.dt),   static_cast<float>(prm.mu),   static_cast<float>(prm.w_cc),
                   static_cast<float>(prm.w_cb), static_cast<float>(prm.a_cc), static_cast<float>(prm.a_cb),
                   static_cast<float>(prm.e_cc), static_cast<float>(prm.e_cb), static_cast<float>(prm.e_bc)};
-  lf_status s = ensure_tiles(m);
-  if (s == LF_OK)
-    s = grow_capacity(m, prm.initial_capacity > 0 ? prm.initial_capacity : std::max<int64_t>(2 * n_v, 4096));
+  // default: three entries per vertex of a tile; the band holds ~1.6 on average
+  const int64_t cap = prm.initial_capacity > 0 ? (prm.initial_capacity + m->num_tiles - 1) / m->num_tiles
+                                               : 3 * lf::kTile;
+  lf_status s = set_tile_cap(m, cap, false);
   if (s == LF_OK) s = upload_job(m);
   if (s != LF_OK) {
     g_create_error = m->err;
@@ -495,11 +478,11 @@ lf_status lf_seed(lf_mesh m, const int32_t* seeds, int32_t k) {
   m->n_layers = k + 1;
   m->h_job.n_layers = k + 1;
   std::memset(&m->h_st, 0, sizeof(m->h_st));
-  LF_CUDA(m, cudaMemcpyAsync(d_seeds, seeds, sizeof(int32_t) * k, cudaMemcpyHostToDevice, m->stream));
-  LF_CUDA(m, cudaMemsetAsync(m->d_st, 0, sizeof(lf::DevStatus), m->stream));
-  LF_CUDA(m, cudaMemsetAsync(m->d_tiles, 0, sizeof(unsigned long long) * m->num_tiles, m->stream));
+  m->h_st.nnz = static_cast<unsigned long long>(m->n_v);
   s = upload_job(m);
+  if (s == LF_OK) s = upload_status(m);
   if (s != LF_OK) return s;
+  LF_CUDA(m, cudaMemcpyAsync(d_seeds, seeds, sizeof(int32_t) * k, cudaMemcpyHostToDevice, m->stream));
   LF_CUDA(m, lf::launch_seed(m->d_job, static_cast<int>(m->n_v), k, d_seeds, m->dtype, m->stream));
   LF_CUDA(m, cudaStreamSynchronize(m->stream));
   m->dfree(d_seeds);
@@ -526,7 +509,7 @@ lf_status lf_step(lf_mesh m, int32_t n_iters) {
       }
     }
     for (; launched < todo; ++launched)
-      LF_CUDA(m, lf::launch_step(m->d_job, m->num_tiles, m->dtype, m->tier, m->stream));
+      LF_CUDA(m, lf::launch_step(m->d_job, m->num_tiles, m->dtype, m->stream));
     s = read_status(m);
     if (s != LF_OK) return s;
     m->steps = static_cast<int64_t>(m->h_st.epoch);
@@ -534,28 +517,14 @@ lf_status lf_step(lf_mesh m, int32_t n_iters) {
 
     // a step failed: the field is intact in buf[epoch & 1]; fix and re-run
     const uint32_t err = m->h_st.err;
-    if (err & lf::ERR_TIMEOUT) {
-      m->poisoned = true;
-      return fail(m, LF_ERR_TIMEOUT, "decoupled look-back wait timed out");
-    }
     if (err & lf::ERR_ZERO_SUM) {
       reset_after_failure(m);
       return fail(m, LF_ERR_STATE, "a vertex summed to zero before normalisation");
     }
-    if (err & lf::ERR_MAP) {
-      if (m->tier + 1 >= lf::kNumTiers) {
-        reset_after_failure(m);
-        return fail(m, LF_ERR_CAPACITY, "a vertex neighbourhood holds more than 160 layers");
-      }
-      ++m->tier;
-      s = ensure_tiles(m);
-      if (s == LF_OK) s = upload_job(m);
-      if (s != LF_OK) return s;
-    }
     if (err & lf::ERR_CAPACITY) {
-      const int64_t need = static_cast<int64_t>(m->h_st.need_nnz);
-      const int64_t grown = std::max<int64_t>(need + need / 4, m->cap + m->cap / 5 + 1);
-      s = grow_capacity(m, grown);
+      const int64_t need = static_cast<int64_t>(m->h_st.need_tile);
+      const int64_t grown = std::max<int64_t>(need + need / 4, m->tile_cap + m->tile_cap / 5 + 1);
+      s = set_tile_cap(m, grown, true);
       if (s != LF_OK) {
         reset_after_failure(m);
         return s;
@@ -592,39 +561,54 @@ lf_status lf_labels(lf_mesh m, int32_t* labels, float* maxval) {
   return LF_OK;
 }
 
+// The current field in plain CSR on the host: the tile segments are copied
+// whole and gathered row by row.
 lf_status lf_get_field(lf_mesh m, int64_t* rowptr, int32_t* layer, float* val, int64_t cap, int64_t* nnz) {
   lf_status s = check_usable(m);
   if (s != LF_OK) return s;
   if (!nnz) return fail(m, LF_ERR_INVALID, "nnz must not be NULL");
   if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed or lf_set_field must come first");
   const int cur = static_cast<int>(m->h_st.epoch & 1u);
-  std::vector<int32_t> rp(static_cast<size_t>(m->n_v) + 1);
-  LF_CUDA(m, cudaMemcpyAsync(rp.data(), m->buf[cur].rowptr, sizeof(int32_t) * (m->n_v + 1), cudaMemcpyDeviceToHost,
+  std::vector<int2> rows(static_cast<size_t>(m->n_v));
+  LF_CUDA(m, cudaMemcpyAsync(rows.data(), m->buf[cur].rows, sizeof(int2) * m->n_v, cudaMemcpyDeviceToHost,
                              m->stream));
   LF_CUDA(m, cudaStreamSynchronize(m->stream));
-  const int64_t total = rp[static_cast<size_t>(m->n_v)];
+  int64_t total = 0;
+  for (int64_t i = 0; i < m->n_v; ++i) {
+    if (rowptr) rowptr[i] = total;
+    total += rows[static_cast<size_t>(i)].y;
+  }
+  if (rowptr) rowptr[m->n_v] = total;
   *nnz = total;
-  if (rowptr)
-    for (int64_t i = 0; i <= m->n_v; ++i) rowptr[i] = rp[static_cast<size_t>(i)];
-  if (!layer || !val || cap < total) return LF_OK;
-  if (total == 0) return LF_OK;
-  std::vector<uint16_t> ids(static_cast<size_t>(total));
-  LF_CUDA(m, cudaMemcpyAsync(ids.data(), m->buf[cur].ids, sizeof(uint16_t) * total, cudaMemcpyDeviceToHost,
+  if (!layer || !val || cap < total || total == 0) return LF_OK;
+  const int64_t entries = m->buffer_entries();
+  std::vector<uint16_t> ids(static_cast<size_t>(entries));
+  std::vector<float> vals(static_cast<size_t>(entries));
+  LF_CUDA(m, cudaMemcpyAsync(ids.data(), m->buf[cur].ids, sizeof(uint16_t) * entries, cudaMemcpyDeviceToHost,
                              m->stream));
   if (m->dtype == LF_F32) {
-    LF_CUDA(m, cudaMemcpyAsync(val, m->buf[cur].vals, sizeof(float) * total, cudaMemcpyDeviceToHost, m->stream));
+    LF_CUDA(m, cudaMemcpyAsync(vals.data(), m->buf[cur].vals, sizeof(float) * entries, cudaMemcpyDeviceToHost,
+                               m->stream));
   } else {
-    if (m->scratch_f_len < total) {
+    if (m->scratch_f_len < entries) {
       m->dfree(m->d_scratch_f);
-      m->d_scratch_f = static_cast<float*>(m->dalloc(sizeof(float) * total));
+      m->d_scratch_f = static_cast<float*>(m->dalloc(sizeof(float) * entries));
       if (!m->d_scratch_f) { m->scratch_f_len = 0; return fail(m, LF_ERR_OOM, "value buffer"); }
-      m->scratch_f_len = total;
+      m->scratch_f_len = entries;
     }
-    LF_CUDA(m, lf::launch_widen(m->buf[cur].vals, m->d_scratch_f, total, m->dtype, m->stream));
-    LF_CUDA(m, cudaMemcpyAsync(val, m->d_scratch_f, sizeof(float) * total, cudaMemcpyDeviceToHost, m->stream));
+    LF_CUDA(m, lf::launch_widen(m->buf[cur].vals, m->d_scratch_f, entries, m->dtype, m->stream));
+    LF_CUDA(m, cudaMemcpyAsync(vals.data(), m->d_scratch_f, sizeof(float) * entries, cudaMemcpyDeviceToHost,
+                               m->stream));
   }
   LF_CUDA(m, cudaStreamSynchronize(m->stream));
-  for (int64_t p = 0; p < total; ++p) layer[p] = ids[static_cast<size_t>(p)];
+  int64_t o = 0;
+  for (int64_t i = 0; i < m->n_v; ++i) {
+    const int2 r = rows[static_cast<size_t>(i)];
+    for (int p = 0; p < r.y; ++p, ++o) {
+      layer[o] = ids[static_cast<size_t>(r.x + p)];
+      val[o] = vals[static_cast<size_t>(r.x + p)];
+    }
+  }
   return LF_OK;
 }
 
@@ -636,48 +620,63 @@ lf_status lf_set_field(lf_mesh m, const int64_t* rowptr, const int32_t* layer, c
   if (n_layers < 2 || n_layers > 65536) return fail(m, LF_ERR_INVALID, "n_layers must be in [2, 65536]");
   if (rowptr[0] != 0 || rowptr[m->n_v] != nnz) return fail(m, LF_ERR_INVALID, "rowptr does not match nnz");
   if (nnz >= kMaxCap) return fail(m, LF_ERR_CAPACITY, "field exceeds 2^31 entries");
-  std::vector<int32_t> rp(static_cast<size_t>(m->n_v) + 1);
-  std::vector<uint16_t> ids(static_cast<size_t>(std::max<int64_t>(nnz, 1)));
+  int64_t need = 0;
   for (int64_t i = 0; i < m->n_v; ++i) {
     if (rowptr[i + 1] < rowptr[i]) return fail(m, LF_ERR_INVALID, "rowptr is not monotone");
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
       if (layer[p] < 0 || layer[p] >= n_layers) return fail(m, LF_ERR_INVALID, "layer out of range");
       if (p > rowptr[i] && layer[p] <= layer[p - 1]) return fail(m, LF_ERR_INVALID, "layers not increasing in a row");
       if (!(val[p] > 0.0f && val[p] <= 1.0f)) return fail(m, LF_ERR_INVALID, "value not in (0, 1]");
-      ids[static_cast<size_t>(p)] = static_cast<uint16_t>(layer[p]);
     }
-    rp[static_cast<size_t>(i)] = static_cast<int32_t>(rowptr[i]);
   }
-  rp[static_cast<size_t>(m->n_v)] = static_cast<int32_t>(nnz);
-  if (nnz > m->cap) {
-    s = grow_capacity(m, nnz + nnz / 4 + 1);
+  for (int t = 0; t < m->num_tiles; ++t) {
+    const int64_t a = static_cast<int64_t>(t) * lf::kTile;
+    const int64_t b = std::min<int64_t>(a + lf::kTile, m->n_v);
+    need = std::max(need, rowptr[b] - rowptr[a]);
+  }
+  if (need > m->tile_cap) {
+    s = set_tile_cap(m, need + need / 4 + 1, false);
     if (s != LF_OK) return s;
   }
-  const int cur = static_cast<int>(m->h_st.epoch & 1u);
-  LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].rowptr, rp.data(), sizeof(int32_t) * (m->n_v + 1), cudaMemcpyHostToDevice,
-                             m->stream));
-  if (nnz > 0) {
-    LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].ids, ids.data(), sizeof(uint16_t) * nnz, cudaMemcpyHostToDevice,
-                               m->stream));
-    if (m->dtype == LF_F32) {
-      LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].vals, val, sizeof(float) * nnz, cudaMemcpyHostToDevice, m->stream));
-    } else {
-      if (m->scratch_f_len < nnz) {
-        m->dfree(m->d_scratch_f);
-        m->d_scratch_f = static_cast<float*>(m->dalloc(sizeof(float) * nnz));
-        if (!m->d_scratch_f) { m->scratch_f_len = 0; return fail(m, LF_ERR_OOM, "value buffer"); }
-        m->scratch_f_len = nnz;
-      }
-      LF_CUDA(m, cudaMemcpyAsync(m->d_scratch_f, val, sizeof(float) * nnz, cudaMemcpyHostToDevice, m->stream));
-      LF_CUDA(m, lf::launch_narrow(m->d_scratch_f, m->buf[cur].vals, nnz, m->dtype, m->stream));
+  // segmented copy: row i of tile t starts at t * tile_cap + (rowptr[i] - rowptr[first row of t])
+  const int64_t entries = m->buffer_entries();
+  std::vector<int2> rows(static_cast<size_t>(m->n_v));
+  std::vector<uint16_t> ids(static_cast<size_t>(entries), 0);
+  std::vector<float> vals(static_cast<size_t>(entries), 0.0f);
+  for (int64_t i = 0; i < m->n_v; ++i) {
+    const int64_t t = i / lf::kTile;
+    const int64_t start = t * m->tile_cap + (rowptr[i] - rowptr[t * lf::kTile]);
+    rows[static_cast<size_t>(i)] = make_int2(static_cast<int>(start), static_cast<int>(rowptr[i + 1] - rowptr[i]));
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      ids[static_cast<size_t>(start + p - rowptr[i])] = static_cast<uint16_t>(layer[p]);
+      vals[static_cast<size_t>(start + p - rowptr[i])] = val[p];
     }
+  }
+  const int cur = static_cast<int>(m->h_st.epoch & 1u);
+  LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].rows, rows.data(), sizeof(int2) * m->n_v, cudaMemcpyHostToDevice,
+                             m->stream));
+  LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].ids, ids.data(), sizeof(uint16_t) * entries, cudaMemcpyHostToDevice,
+                             m->stream));
+  if (m->dtype == LF_F32) {
+    LF_CUDA(m, cudaMemcpyAsync(m->buf[cur].vals, vals.data(), sizeof(float) * entries, cudaMemcpyHostToDevice,
+                               m->stream));
+  } else {
+    if (m->scratch_f_len < entries) {
+      m->dfree(m->d_scratch_f);
+      m->d_scratch_f = static_cast<float*>(m->dalloc(sizeof(float) * entries));
+      if (!m->d_scratch_f) { m->scratch_f_len = 0; return fail(m, LF_ERR_OOM, "value buffer"); }
+      m->scratch_f_len = entries;
+    }
+    LF_CUDA(m, cudaMemcpyAsync(m->d_scratch_f, vals.data(), sizeof(float) * entries, cudaMemcpyHostToDevice,
+                               m->stream));
+    LF_CUDA(m, lf::launch_narrow(m->d_scratch_f, m->buf[cur].vals, entries, m->dtype, m->stream));
   }
   m->n_layers = n_layers;
   m->h_job.n_layers = n_layers;
+  m->h_st.nnz = static_cast<unsigned long long>(nnz);
   s = upload_job(m);
-  if (s != LF_OK) return s;
-  LF_CUDA(m, cudaStreamSynchronize(m->stream));
-  return LF_OK;
+  if (s == LF_OK) s = upload_status(m);
+  return s;
 }
 
 lf_status lf_stats(lf_mesh m, lf_stats_t* out) {
@@ -690,23 +689,16 @@ lf_status lf_stats(lf_mesh m, lf_stats_t* out) {
   out->n_v = m->n_v;
   out->n_layers = m->n_layers;
   out->steps = m->steps;
-  out->capacity = m->cap;
+  out->nnz = m->n_layers > 0 ? static_cast<int64_t>(m->h_st.nnz) : 0;
+  out->capacity = m->buffer_entries();
   out->operator_nnz = m->L_nnz;
   out->skeleton_total = m->h_st.skeleton_total;
   out->nnz_io_total = m->h_st.nnz_io_total;
   out->device_bytes = m->device_bytes;
   out->retries = m->retries;
-  out->map_slots = lf::kTiers[m->tier].map_slots;
+  out->map_slots = lf::step_slots();
   out->field_dtype = m->dtype;
   out->value_bytes = lf::value_bytes(m->dtype);
-  if (m->n_layers > 0 && !m->poisoned) {
-    int32_t nnz = 0;
-    const int cur = static_cast<int>(m->h_st.epoch & 1u);
-    LF_CUDA(m, cudaMemcpyAsync(&nnz, m->buf[cur].rowptr + m->n_v, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                               m->stream));
-    LF_CUDA(m, cudaStreamSynchronize(m->stream));
-    out->nnz = nnz;
-  }
   return LF_OK;
 }
 

@@ -9,9 +9,7 @@ namespace lf {
 
 // Error bits raised on the device (DevStatus::err).
 enum : uint32_t {
-  ERR_CAPACITY = 1u,   // the output field would exceed the buffer capacity
-  ERR_MAP = 2u,        // a vertex's layer union exceeded the map slots
-  ERR_TIMEOUT = 4u,    // a bounded wait in the decoupled look-back gave up
+  ERR_CAPACITY = 1u,   // a tile's output would exceed its segment of the field buffer
   ERR_ZERO_SUM = 8u,   // a vertex summed to zero before normalisation
 };
 
@@ -21,23 +19,26 @@ enum : uint32_t {
 struct DevStatus {
   uint32_t err;
   uint32_t epoch;
-  uint32_t ticket;                    // next tile of the running step
   uint32_t done;                      // CTAs finished in the running step
-  unsigned long long need_nnz;        // capacity asked for by failing tiles
-  uint32_t need_map;                  // nonzero when ERR_MAP was raised
   uint32_t pad0;
+  unsigned long long need_tile;       // entries asked for by the fullest failing tile
   unsigned long long skeleton_total;  // sum of |skeleton| over completed steps
   unsigned long long skeleton_step;   // running step, summed over tiles
   unsigned long long nnz_io_total;    // sum of nnz(in) + nnz(out), completed steps
-  unsigned long long pad1;
+  unsigned long long nnz_io_step;     // running step
+  unsigned long long nnz_step;        // nnz(out) of the running step
+  unsigned long long nnz;             // nnz of the current field
 };
-static_assert(sizeof(DevStatus) == 64, "DevStatus layout");
+static_assert(sizeof(DevStatus) == 72, "DevStatus layout");
 
-// One CSR copy of the field: rows = vertices, entries sorted by layer id.
+// One copy of the field in tile-segmented CSR.  Vertex i belongs to tile
+// i / kTile; the rows of a tile are stored one after another, ids ascending
+// within a row, in the segment [tile * tile_cap, (tile + 1) * tile_cap) of ids
+// and vals.  rows[i] = (start, count) of row i.
 struct FieldBuf {
-  int32_t* rowptr;   // n_v + 1
-  uint16_t* ids;     // capacity
-  void* vals;        // capacity values of the storage type
+  int2* rows;        // n_v
+  uint16_t* ids;     // num_tiles * tile_cap
+  void* vals;        // num_tiles * tile_cap values of the storage type
 };
 
 struct Coefs {
@@ -50,34 +51,31 @@ struct JobDesc {
   int32_t n_v;
   int32_t n_layers;          // k + 1; the base layer is n_layers - 1
   int32_t num_tiles;         // CTAs of one step launch
-  int32_t cap;               // entries per field buffer
+  int32_t tile_cap;          // entries per tile segment (multiple of 16)
   const int32_t* L_rowptr;   // n_v + 1, off-diagonal entries only
   const int2* L_colval;      // (column, float bits of L_ij), j != i
   FieldBuf buf[2];
   DevStatus* st;
-  unsigned long long* tile_status;   // num_tiles look-back words
   Coefs c;
   int32_t pad[3];
 };
 
-// Step kernel variants: map slots per vertex and threads per CTA.
-struct StepTier {
-  int map_slots;
-  int block;
-};
-constexpr int kNumTiers = 3;
-extern const StepTier kTiers[kNumTiers];
+constexpr int kTile = 256;   // vertices per tile = threads per step CTA
 
-// Returns the kernel entry for (dtype, tier) and its dynamic shared memory.
-const void* step_kernel(int dtype, int tier, size_t* smem_bytes);
-// Sets the shared-memory attribute of every step kernel variant.
-cudaError_t init_kernels();
-
-cudaError_t launch_step(const JobDesc* d_job, int num_tiles, int dtype, int tier, cudaStream_t s);
+// Register slots of the step kernel's fast path.
+int step_slots();
+// Kernel entry of the step for a storage type (0 f32, 1 bf16, 2 f16).
+const void* step_kernel(int dtype);
+// One step launch with programmatic stream serialisation.
+cudaError_t launch_step(const JobDesc* d_job, int num_tiles, int dtype, cudaStream_t s);
 cudaError_t launch_seed(const JobDesc* d_job, int n_v, int k, const int32_t* d_seeds, int dtype,
                         cudaStream_t s);
 cudaError_t launch_labels(const JobDesc* d_job, int n_v, int dtype, int32_t* d_labels, float* d_maxval,
                           cudaStream_t s);
+// Copies the rows of `from` into the segments of `to` (tile_cap may differ).
+cudaError_t launch_relayout(const int2* rows_from, const uint16_t* ids_from, const void* vals_from,
+                            int cap_from, int2* rows_to, uint16_t* ids_to, void* vals_to, int cap_to,
+                            int n_v, int dtype, cudaStream_t s);
 // Converts between the storage type and float on the device.
 cudaError_t launch_widen(const void* src, float* dst, int64_t n, int dtype, cudaStream_t s);
 cudaError_t launch_narrow(const float* src, void* dst, int64_t n, int dtype, cudaStream_t s);

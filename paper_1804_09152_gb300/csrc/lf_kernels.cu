@@ -3,15 +3,19 @@
 // One thread owns one vertex i.  It gathers the closed neighbourhood of i
 // from L (CSR, off-diagonal only) and the field F (CSR, layer ids sorted),
 // accumulating G = L F (the paper's L_t = Phi L^T, Algorithm 1) per layer in
-// a small per-thread map in shared memory; applies the interest-skeleton
-// test, the explicit Euler update of Eq. 11-13 in closed form, the clamp and
-// the normalisation (Sec. 4); and writes the surviving entries of row i into
-// the output CSR.  Row offsets come from a single-pass scan with decoupled
-// look-back (Merrill and Garland, 2016) over tiles of one CTA each, so the
-// whole iteration is one launch with no host round trip.
+// a four-slot register map; applies the interest-skeleton test, the explicit
+// Euler update of Eq. 11-13 in closed form, the clamp and the normalisation
+// (Sec. 4); and writes the surviving entries of row i into the output CSR.
+// A vertex whose neighbourhood holds more layers than the map takes a slow
+// path that enumerates the layer union in increasing id order by repeated
+// minimum search over the same rows, so any union size is exact without
+// extra storage.
 //
-// Every wait in this file is bounded by the global timer; a wait that runs
-// out raises ERR_TIMEOUT, poisons its tile and lets the kernel finish.
+// The field is a tile-segmented CSR: the 256 vertices of a tile (one CTA)
+// write their rows one after another into the tile's own segment, row
+// offsets coming from a block-wide prefix sum of the row lengths.  No CTA
+// waits for another, so one launch is one iteration with no host round trip;
+// consecutive launches overlap through programmatic dependent launch.
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -21,8 +25,6 @@
 #include "lf_internal.h"
 
 namespace lf {
-
-const StepTier kTiers[kNumTiers] = {{16, 256}, {48, 128}, {160, 32}};
 
 namespace {
 
@@ -50,304 +52,473 @@ template <> struct Val<2> {
 };
 
 // ---------------------------------------------------------------------------
-// device-scope relaxed atomics and the global timer
+// device-scope relaxed accesses and dependent-launch control
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
+// Waits until the previous kernel in the stream has completed and its writes
+// are visible (no-op when the launch carries no programmatic dependency).
+__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel in the stream start launching its CTAs.
+__device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+constexpr int kBlock = kTile;   // threads (= vertices) per CTA
+constexpr int kSlots = 6;       // register map slots of the fast path
+constexpr int kOwn = 4;         // own-row entries the fast path accepts
+constexpr int kChunk = 4;       // neighbours fetched per batch
+
+// Per-vertex quantities of the closed-form update (class coefficients).
+struct VertexSums {
+  float sG, sF, r, Gb, Fb, sqFb;
+  int nC, hasb;
+};
+
+// d for one skeleton entry, then the Euler step and the clamp.  With S the
+// skeleton, A_j = sum_{l in S} a_jl G_l and W_j = sum_{l in S} w_jl F_l,
+// Algorithm 1's double sum is -(mu/n)[1/2 (n A_j - sum A) + (n W_j - sum W)]
+// and its band term (mu/n) sqrt(F_j) sum_k e_jk sqrt(F_k).
+struct Update {
+  float fn, fnc, sumA, sumW, mun, sqFb;
+  __device__ __forceinline__ Update(const VertexSums& s, const Coefs& c) {
+    const int n = s.nC + s.hasb;
+    fn = static_cast<float>(n);
+    fnc = static_cast<float>(s.nC);
+    sumA = c.a_cc * (fnc - 1.0f) * s.sG + (s.hasb ? c.a_cb * (fnc * s.Gb + s.sG) : 0.0f);
+    sumW = c.w_cc * (fnc - 1.0f) * s.sF + (s.hasb ? c.w_cb * (fnc * s.Fb + s.sF) : 0.0f);
+    mun = c.mu / fn;
+    sqFb = s.sqFb;
+  }
+  // f, g: F and G of the entry; sqf = sqrt(f), computed once by the caller.
+  __device__ __forceinline__ float value(bool is_base, float f, float g, float sqf, const VertexSums& s,
+                                         const Coefs& c) const {
+    float A, W, R;
+    if (is_base) {
+      A = c.a_cb * s.sG;
+      W = c.w_cb * s.sF;
+      R = c.e_bc * s.r;
+    } else {
+      A = c.a_cc * (s.sG - g) + (s.hasb ? c.a_cb * s.Gb : 0.0f);
+      W = c.w_cc * (s.sF - f) + (s.hasb ? c.w_cb * s.Fb : 0.0f);
+      R = c.e_cc * (s.r - sqf) + (s.hasb ? c.e_cb * sqFb : 0.0f);
+    }
+    const float d = -mun * (0.5f * (fn * A - sumA) + (fn * W - sumW)) + mun * sqf * R;
+    float v = f + d * c.dt;
+    if (v > 1.0f) v = 1.0f;
+    if (v <= 0.0f) v = 0.0f;
+    return v;
+  }
+};
+
+__device__ __forceinline__ bool in_skeleton(float f, float g) { return f > 0.0f || (f == 0.0f && g > 0.0f); }
+
+__device__ __forceinline__ void add_to_sums(VertexSums& s, bool is_base, float f, float g, float sqf) {
+  if (is_base) {
+    s.hasb = 1;
+    s.Gb = g;
+    s.Fb = f;
+    s.sqFb = sqf;
+  } else {
+    s.sG += g;
+    s.sF += f;
+    s.r += sqf;
+    ++s.nC;
+  }
 }
 
-// Look-back status word: value in bits 0-31, flag in bits 32-33, tag in 34-63.
-constexpr unsigned long long kFlagAgg = 1ull, kFlagPrefix = 2ull, kFlagPoison = 3ull;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
 
-__device__ __forceinline__ unsigned long long pack_status(uint32_t tag, unsigned long long flag, uint32_t v) {
-  return (static_cast<unsigned long long>(tag) << 34) | (flag << 32) | v;
+// The closed neighbourhood of one vertex, read straight from global memory.
+// Used by the slow path, which enumerates the layer union in increasing id
+// order: next_layer() scans the sorted rows for the smallest id above `cur`,
+// sums() accumulates G and F of one layer in the order of the row of L.
+template <int DT>
+struct Neighbourhood {
+  using V = Val<DT>;
+  using T = typename V::T;
+  const int2* __restrict__ rows;
+  const uint16_t* __restrict__ Fid;
+  const T* __restrict__ Fval;
+  const int2* __restrict__ Lcv;
+  int p0, p1, q0, q1;
+  float dsum;
+
+  __device__ int next_layer(int cur) const {
+    int nx = 0x7fffffff;
+    for (int p = p0; p < p1; ++p) {
+      const int l = __ldg(Fid + p);
+      if (l > cur) { nx = min(nx, l); break; }
+    }
+    for (int q = q0; q < q1; ++q) {
+      const int2 rj = __ldg(rows + __ldg(&Lcv[q].x));
+      for (int p = rj.x; p < rj.x + rj.y; ++p) {
+        const int l = __ldg(Fid + p);
+        if (l > cur) { nx = min(nx, l); break; }
+      }
+    }
+    return nx;
+  }
+
+  __device__ void sums(int lay, float& G, float& F) const {
+    F = 0.0f;
+    G = 0.0f;
+    for (int p = p0; p < p1; ++p) {
+      const int l = __ldg(Fid + p);
+      if (l == lay) { F = V::load(Fval + p); break; }
+      if (l > lay) break;
+    }
+    for (int q = q0; q < q1; ++q) {
+      const int2 cv = __ldg(Lcv + q);
+      const float lij = __int_as_float(cv.y);
+      const int2 rj = __ldg(rows + cv.x);
+      for (int p = rj.x; p < rj.x + rj.y; ++p) {
+        const int l = __ldg(Fid + p);
+        if (l == lay) { G += lij * V::load(Fval + p); break; }
+        if (l > lay) break;
+      }
+    }
+    G = fmaf(-dsum, F, G);        // diagonal: L_ii = -sum_{j != i} L_ij
+  }
+};
+
+// Register map of the fast path: layer id (-1 = empty) and G per slot; F is
+// kept for the first kOwn slots, which hold the vertex's own row (the other
+// slots are layers absent from it, F = 0).
+struct SlotMap {
+  int id[kSlots];
+  float g[kSlots];
+  float f[kOwn];
+  int cnt;
+
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) { id[s] = -1; g[s] = 0.0f; }
+#pragma unroll
+    for (int s = 0; s < kOwn; ++s) f[s] = 0.0f;
+    cnt = 0;
+  }
+  __device__ __forceinline__ float fv(int s) const { return s < kOwn ? f[s < kOwn ? s : 0] : 0.0f; }
+  // Adds x to the slot of layer l, opening a slot if needed.  False when full.
+  __device__ __forceinline__ bool add(int l, float x) {
+    bool found = false;
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      if (s < cnt && !found && id[s] == l) { g[s] += x; found = true; }
+    }
+    if (found) return true;
+    if (cnt >= kSlots) return false;
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      if (s == cnt) { id[s] = l; g[s] = x; }
+    }
+    ++cnt;
+    return true;
+  }
+};
+
+// Block-wide sum of one value per thread (all threads get the result).
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  unsigned s = 0;
+#pragma unroll
+  for (int w = 0; w < kBlock / 32; ++w) s += s_red[w];
+  __syncthreads();
+  return s;
 }
 
 // ---------------------------------------------------------------------------
 // the step kernel
 // ---------------------------------------------------------------------------
-template <int DT, int M, int B>
-__global__ void __launch_bounds__(B) step_kernel_impl(const JobDesc* __restrict__ job) {
+template <int DT>
+__global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __restrict__ job) {
   using V = Val<DT>;
   using T = typename V::T;
-  constexpr int kWarps = B / 32;
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* s_g = reinterpret_cast<float*>(smem);                 // [M][B] G, then new value
-  float* s_f = s_g + M * B;                                    // [M][B] F before the step
-  uint16_t* s_id = reinterpret_cast<uint16_t*>(s_f + M * B);   // [M][B] layer ids
-  __shared__ uint32_t s_tile, s_epoch, s_abort, s_prefix, s_fail;
+  constexpr int kWarps = kBlock / 32;
+  __shared__ uint32_t s_epoch, s_abort;
+  __shared__ unsigned s_red[kWarps];
   __shared__ int s_warp_cnt[kWarps];
-  __shared__ int s_warp_sk[kWarps];
+
+  wait_previous_grid();
+  allow_next_grid();
 
   const int t = threadIdx.x;
   const int lane = t & 31;
   const int warp = t >> 5;
   DevStatus* st = job->st;
-
   if (t == 0) {
-    const uint32_t e = ld_relaxed_u32(&st->err);
-    s_abort = e;
-    if (e == 0u) {
-      s_tile = atomicAdd(&st->ticket, 1u);
-      s_epoch = ld_relaxed_u32(&st->epoch);
-    }
+    s_abort = ld_relaxed_u32(&st->err);
+    s_epoch = ld_relaxed_u32(&st->epoch);
   }
   __syncthreads();
   if (s_abort) return;
 
-  const uint32_t tile = s_tile;
+  const int tile = blockIdx.x;
   const uint32_t epoch = s_epoch;
   const int n_v = job->n_v;
   const int base = job->n_layers - 1;
+  const int cap = job->tile_cap;
   const FieldBuf in = job->buf[epoch & 1u];
   const FieldBuf out = job->buf[(epoch & 1u) ^ 1u];
-  const int32_t* __restrict__ Frp = in.rowptr;
-  const uint16_t* __restrict__ Fid = in.ids;
-  const T* __restrict__ Fval = static_cast<const T*>(in.vals);
   const Coefs c = job->c;
 
-  const int i = static_cast<int>(tile) * B + t;
-  int cnt = 0;      // distinct layers seen in the closed neighbourhood
-  int kept = 0;     // entries of the output row
-  int nsk = 0;      // |interest skeleton| of the row
-  bool map_ovf = false, zero_sum = false;
+  Neighbourhood<DT> nb;
+  nb.rows = in.rows;
+  nb.Fid = in.ids;
+  nb.Fval = static_cast<const T*>(in.vals);
+  nb.Lcv = job->L_colval;
+  nb.dsum = 0.0f;
+
+  const int i = tile * kBlock + t;
+  SlotMap mp;
+  mp.clear();
+  bool slow = false, zero_sum = false;
+  int kept = 0, nsk = 0, own = 0;
+  float vnew[kSlots];
+  bool keep[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) { vnew[s] = 0.0f; keep[s] = false; }
+  VertexSums S = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, 0};
+  float tot = 0.0f;
 
   if (i < n_v) {
-    // ---- own row: F(i, .) -------------------------------------------------
-    const int p0 = __ldg(Frp + i), p1 = __ldg(Frp + i + 1);
-    for (int p = p0; p < p1; ++p) {
-      if (cnt == M) { map_ovf = true; break; }
-      s_id[cnt * B + t] = __ldg(Fid + p);
-      s_f[cnt * B + t] = V::load(Fval + p);
-      s_g[cnt * B + t] = 0.0f;
-      ++cnt;
-    }
-    const int own = cnt;
-    // ---- G = sum_j L_ij F(j, .) over the off-diagonal entries of row i ----
-    float dsum = 0.0f;
-    const int q0 = __ldg(job->L_rowptr + i), q1 = __ldg(job->L_rowptr + i + 1);
-    for (int q = q0; q < q1 && !map_ovf; ++q) {
-      const int2 cv = __ldg(job->L_colval + q);
-      const int j = cv.x;
-      const float lij = __int_as_float(cv.y);
-      dsum += lij;
-      const int r0 = __ldg(Frp + j), r1 = __ldg(Frp + j + 1);
-      for (int p = r0; p < r1; ++p) {
-        const uint16_t l = __ldg(Fid + p);
-        const float x = lij * V::load(Fval + p);
-        int s = 0;
-        while (s < cnt && s_id[s * B + t] != l) ++s;
-        if (s < cnt) {
-          s_g[s * B + t] += x;
-        } else if (cnt < M) {
-          s_id[cnt * B + t] = l;
-          s_g[cnt * B + t] = x;
-          s_f[cnt * B + t] = 0.0f;
-          ++cnt;
-        } else {
-          map_ovf = true;
-          break;
+    const int2 ri = __ldg(nb.rows + i);
+    nb.p0 = ri.x;
+    nb.p1 = ri.x + ri.y;
+    own = ri.y;
+    nb.q0 = __ldg(job->L_rowptr + i);
+    nb.q1 = __ldg(job->L_rowptr + i + 1);
+    if (own > kOwn) {
+      slow = true;
+    } else {
+#pragma unroll
+      for (int s = 0; s < kOwn; ++s) {
+        if (s < own) {
+          mp.id[s] = __ldg(nb.Fid + nb.p0 + s);
+          mp.f[s] = V::load(nb.Fval + nb.p0 + s);
         }
       }
+      mp.cnt = own;
     }
-    // diagonal: L_ii = -sum_{j != i} L_ij
-    for (int s = 0; s < own; ++s) s_g[s * B + t] = fmaf(-dsum, s_f[s * B + t], s_g[s * B + t]);
+    // ---- G = sum_j L_ij F(j, .): neighbours in batches of kChunk; the first
+    // two entries of every row in the batch are loaded before any is used
+    for (int qb = nb.q0; qb < nb.q1; qb += kChunk) {
+      int jj[kChunk], r0[kChunk], rn[kChunk];
+      float lij[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        jj[k] = -1;
+        lij[k] = 0.0f;
+        if (qb + k < nb.q1) {
+          const int2 cv = __ldg(nb.Lcv + qb + k);
+          jj[k] = cv.x;
+          lij[k] = __int_as_float(cv.y);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        r0[k] = rn[k] = 0;
+        if (jj[k] >= 0) {
+          const int2 rj = __ldg(nb.rows + jj[k]);
+          r0[k] = rj.x;
+          rn[k] = rj.y;
+          nb.dsum += lij[k];
+        }
+      }
+      if (slow) continue;
+      // the first two entries of each row of the batch; -2 marks "no entry"
+      constexpr int kE = 2 * kChunk;
+      int eid[kE];
+      float ex[kE];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        eid[2 * k] = eid[2 * k + 1] = -2;
+        ex[2 * k] = ex[2 * k + 1] = 0.0f;
+        if (rn[k] > 0) {
+          eid[2 * k] = __ldg(nb.Fid + r0[k]);
+          ex[2 * k] = lij[k] * V::load(nb.Fval + r0[k]);
+        }
+        if (rn[k] > 1) {
+          eid[2 * k + 1] = __ldg(nb.Fid + r0[k] + 1);
+          ex[2 * k + 1] = lij[k] * V::load(nb.Fval + r0[k] + 1);
+        }
+      }
+      // entries whose layer already has a slot: slot x entry compare matrix,
+      // each slot summing its entries in entry order (empty slots hold -1)
+      bool hit[kE];
+#pragma unroll
+      for (int e = 0; e < kE; ++e) hit[e] = eid[e] < 0;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+#pragma unroll
+        for (int e = 0; e < kE; ++e) {
+          const bool m = eid[e] == mp.id[s];
+          mp.g[s] = m ? mp.g[s] + ex[e] : mp.g[s];
+          hit[e] = hit[e] || m;
+        }
+      }
+      // layers new to the map, in entry order (rare)
+      bool all_hit = true;
+#pragma unroll
+      for (int e = 0; e < kE; ++e) all_hit = all_hit && hit[e];
+      if (!all_hit) {
+#pragma unroll
+        for (int e = 0; e < kE; ++e)
+          if (!hit[e] && !mp.add(eid[e], ex[e])) slow = true;
+      }
+      // rows with more than two entries
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        for (int p = r0[k] + 2; p < r0[k] + rn[k] && !slow; ++p)
+          if (!mp.add(__ldg(nb.Fid + p), lij[k] * V::load(nb.Fval + p))) slow = true;
+    }
 
-    if (!map_ovf) {
-      // ---- interest skeleton and per-vertex sums (class coefficients) -----
-      float sG = 0.0f, sF = 0.0f, r = 0.0f, Gb = 0.0f, Fb = 0.0f;
-      int nC = 0, hasb = 0;
-      for (int s = 0; s < cnt; ++s) {
-        const float f = s_f[s * B + t], g = s_g[s * B + t];
-        const bool in_sk = (f > 0.0f) || (f == 0.0f && g > 0.0f);
-        if (!in_sk) { s_f[s * B + t] = -1.0f; continue; }   // marks "not in skeleton"
-        if (s_id[s * B + t] == base) { hasb = 1; Gb = g; Fb = f; }
-        else { sG += g; sF += f; r += sqrtf(f); ++nC; }
-      }
-      const int n = nC + hasb;
-      nsk = n;
-      const float fn = static_cast<float>(n);
-      const float fnc = static_cast<float>(nC);
-      const float sumA = c.a_cc * (fnc - 1.0f) * sG + (hasb ? c.a_cb * (fnc * Gb + sG) : 0.0f);
-      const float sumW = c.w_cc * (fnc - 1.0f) * sF + (hasb ? c.w_cb * (fnc * Fb + sF) : 0.0f);
-      const float mun = c.mu / fn;
-      const float sqFb = sqrtf(Fb);
-      float tot = 0.0f;
-      for (int s = 0; s < cnt; ++s) {
-        const float f = s_f[s * B + t];
-        if (f < 0.0f) continue;
-        const float g = s_g[s * B + t];
-        float A, W, R;
-        if (s_id[s * B + t] == base) {
-          A = c.a_cb * sG;
-          W = c.w_cb * sF;
-          R = c.e_bc * r;
-        } else {
-          A = c.a_cc * (sG - g) + (hasb ? c.a_cb * Gb : 0.0f);
-          W = c.w_cc * (sF - f) + (hasb ? c.w_cb * Fb : 0.0f);
-          R = c.e_cc * (r - sqrtf(f)) + (hasb ? c.e_cb * sqFb : 0.0f);
+    if (!slow) {
+      // ---- fast path: diagonal, skeleton, update over the register map ------
+#pragma unroll
+      for (int s = 0; s < kOwn; ++s)
+        if (s < own) mp.g[s] = fmaf(-nb.dsum, mp.f[s], mp.g[s]);
+      float sq[kOwn];
+#pragma unroll
+      for (int s = 0; s < kOwn; ++s) sq[s] = (s < own) ? sqrtf(mp.f[s]) : 0.0f;
+      bool ins[kSlots];
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) ins[s] = false;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        if (s < mp.cnt) {
+          ins[s] = in_skeleton(mp.fv(s), mp.g[s]);
+          if (ins[s]) add_to_sums(S, mp.id[s] == base, mp.fv(s), mp.g[s], s < kOwn ? sq[s < kOwn ? s : 0] : 0.0f);
         }
-        const float d = -mun * (0.5f * (fn * A - sumA) + (fn * W - sumW)) + mun * sqrtf(f) * R;
-        float v = f + d * c.dt;
-        if (v > 1.0f) v = 1.0f;
-        if (v <= 0.0f) v = 0.0f;
-        s_g[s * B + t] = v;
-        tot += v;
+      }
+      const Update U(S, c);
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        if (s < mp.cnt && ins[s]) {
+          vnew[s] = U.value(mp.id[s] == base, mp.fv(s), mp.g[s], s < kOwn ? sq[s < kOwn ? s : 0] : 0.0f, S, c);
+          tot += vnew[s];
+        }
       }
       if (!(tot > 0.0f)) zero_sum = true;
-      // ---- normalise, round to the storage type, drop zeros ----------------
-      for (int s = 0; s < cnt; ++s) {
-        if (s_f[s * B + t] < 0.0f) continue;
-        const float vs = V::widen(V::round(s_g[s * B + t] / tot));
-        if (vs != 0.0f) { s_g[s * B + t] = vs; ++kept; }
-        else s_f[s * B + t] = -1.0f;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        if (s < mp.cnt && ins[s]) {
+          const float vs = V::widen(V::round(vnew[s] / tot));
+          if (vs != 0.0f) { keep[s] = true; vnew[s] = vs; ++kept; }
+        }
       }
-      if (zero_sum) kept = 0;
+    } else {
+      // ---- slow path: the union in increasing id order, three passes -------
+      float G, F;
+      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+        nb.sums(l, G, F);
+        if (in_skeleton(F, G)) add_to_sums(S, l == base, F, G, sqrtf(F));
+      }
+      const Update U(S, c);
+      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+        nb.sums(l, G, F);
+        if (in_skeleton(F, G)) tot += U.value(l == base, F, G, sqrtf(F), S, c);
+      }
+      if (!(tot > 0.0f)) zero_sum = true;
+      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+        nb.sums(l, G, F);
+        if (in_skeleton(F, G) && V::widen(V::round(U.value(l == base, F, G, sqrtf(F), S, c) / tot)) != 0.0f)
+          ++kept;
+      }
     }
+    nsk = S.nC + S.hasb;
+    if (zero_sum) kept = 0;
   }
 
-  // ---- tile scan of the output row lengths ---------------------------------
-  int x = map_ovf ? 0 : kept;
-  int sk = nsk;
+  // ---- block scan of the output row lengths: offsets inside the segment ----
+  int x = kept;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
-    sk += __shfl_xor_sync(0xffffffffu, sk, o);
   }
   if (lane == 31) s_warp_cnt[warp] = x;
-  if (lane == 0) s_warp_sk[warp] = sk;
-  const bool bad_map = __syncthreads_or(map_ovf);
   const bool bad_sum = __syncthreads_or(zero_sum);
-  int warp_off = 0, tile_total = 0, tile_sk = 0;
+  int warp_off = 0, tile_total = 0;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) {
     if (w < warp) warp_off += s_warp_cnt[w];
     tile_total += s_warp_cnt[w];
-    tile_sk += s_warp_sk[w];
   }
-  const int local_excl = warp_off + x - (map_ovf ? 0 : kept);
+  const int local_excl = warp_off + x - kept;
+  const unsigned tile_sk = block_sum(static_cast<unsigned>(nsk), s_red);
+  const unsigned tile_io = block_sum(static_cast<unsigned>(own + kept), s_red);
 
-  // ---- decoupled look-back: exclusive prefix of this tile ------------------
-  if (warp == 0) {
-    unsigned long long* ts = job->tile_status;
-    const uint32_t tag = (epoch + 1u) & 0x3fffffffu;
-    uint32_t excl = 0;
-    bool fail = false;
-    if (tile == 0) {
-      if (lane == 0) st_relaxed(ts, pack_status(tag, kFlagPrefix, static_cast<uint32_t>(tile_total)));
-    } else {
-      if (lane == 0) st_relaxed(ts + tile, pack_status(tag, kFlagAgg, static_cast<uint32_t>(tile_total)));
-      int pred = static_cast<int>(tile) - 1 - lane;
-      const unsigned long long t0 = global_ns();
-      while (true) {
-        unsigned long long w = 0ull, flag = kFlagPrefix;
-        uint32_t val = 0u;
-        bool timed_out = false;
-        if (pred >= 0) {
-          unsigned int ns = 32;
-          while (true) {
-            w = ld_relaxed(ts + pred);
-            flag = (w >> 32) & 3ull;
-            if ((w >> 34) == tag && flag != 0ull) break;
-            if (global_ns() - t0 > kWaitLimitNs) { timed_out = true; break; }
-            __nanosleep(ns);
-            if (ns < 1024) ns <<= 1;
-          }
-          val = static_cast<uint32_t>(w);
-        }
-        const bool poisoned = timed_out || flag == kFlagPoison;
-        if (__any_sync(0xffffffffu, poisoned)) { fail = true; break; }
-        const unsigned pm = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
-        const int first = __ffs(pm) - 1;                 // closest tile with a full prefix
-        uint32_t contrib = (pm == 0u || lane <= first) ? val : 0u;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
-        excl += contrib;
-        if (pm != 0u) break;
-        pred -= 32;
-      }
-      if (lane == 0) {
-        if (fail) {
-          st_relaxed(ts + tile, pack_status(tag, kFlagPoison, 0u));
-          atomicOr(&st->err, ERR_TIMEOUT);
-        } else {
-          st_relaxed(ts + tile, pack_status(tag, kFlagPrefix, excl + static_cast<uint32_t>(tile_total)));
-        }
-      }
-    }
-    if (lane == 0) {
-      s_prefix = excl;
-      s_fail = fail ? 1u : 0u;
-    }
-  }
-  __syncthreads();
-
-  const unsigned long long row0 = s_prefix;
-  const unsigned long long tile_end = row0 + static_cast<unsigned long long>(tile_total);
-  bool write = !s_fail && !bad_map && !bad_sum;
-  if (t == 0) {
-    if (bad_map) { atomicOr(&st->err, ERR_MAP); atomicMax(&st->need_map, 1u); }
-    if (bad_sum) atomicOr(&st->err, ERR_ZERO_SUM);
-  }
-  if (write && tile_end > static_cast<unsigned long long>(job->cap)) {
+  bool write = !bad_sum;
+  if (t == 0 && bad_sum) atomicOr(&st->err, ERR_ZERO_SUM);
+  if (write && tile_total > cap) {
     write = false;
     if (t == 0) {
       atomicOr(&st->err, ERR_CAPACITY);
-      atomicMax(&st->need_nnz, tile_end);
+      atomicMax(&st->need_tile, static_cast<unsigned long long>(tile_total));
     }
   }
 
   // ---- write row i of the output, entries sorted by layer id ---------------
   if (write && i < n_v) {
-    const int off = static_cast<int>(row0) + local_excl;
-    out.rowptr[i] = off;
-    if (i == n_v - 1) out.rowptr[n_v] = off + kept;
+    const int off = tile * cap + local_excl;
+    out.rows[i] = make_int2(off, kept);
     T* ov = static_cast<T*>(out.vals);
-    for (int s = 0; s < cnt; ++s) {
-      if (s_f[s * B + t] < 0.0f) continue;
-      const uint16_t l = s_id[s * B + t];
-      int rank = 0;
-      for (int u = 0; u < cnt; ++u)
-        rank += (s_f[u * B + t] >= 0.0f && s_id[u * B + t] < l) ? 1 : 0;
-      out.ids[off + rank] = l;
-      ov[off + rank] = V::round(s_g[s * B + t]);
+    if (!slow) {
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        if (s >= mp.cnt || !keep[s]) continue;
+        int rank = 0;
+#pragma unroll
+        for (int u = 0; u < kSlots; ++u)
+          if (u < mp.cnt) rank += (keep[u] && mp.id[u] < mp.id[s]) ? 1 : 0;
+        out.ids[off + rank] = static_cast<uint16_t>(mp.id[s]);
+        ov[off + rank] = V::round(vnew[s]);
+      }
+    } else {
+      const Update U(S, c);
+      float G, F;
+      int o = off;
+      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+        nb.sums(l, G, F);
+        if (!in_skeleton(F, G)) continue;
+        const T vt = V::round(U.value(l == base, F, G, sqrtf(F), S, c) / tot);
+        if (V::widen(vt) != 0.0f) {
+          out.ids[o] = static_cast<uint16_t>(l);
+          ov[o] = vt;
+          ++o;
+        }
+      }
     }
   }
 
   // ---- end of step: the last CTA commits the step ---------------------------
-  __syncthreads();
   if (t == 0) {
     atomicAdd(&st->skeleton_step, static_cast<unsigned long long>(tile_sk));
+    atomicAdd(&st->nnz_io_step, static_cast<unsigned long long>(tile_io));
+    atomicAdd(&st->nnz_step, static_cast<unsigned long long>(tile_total));
     __threadfence();
     const uint32_t prev = atomicAdd(&st->done, 1u);
     if (prev == gridDim.x - 1u) {
       __threadfence();
       if (ld_relaxed_u32(&st->err) == 0u) {
-        const unsigned long long nin = static_cast<unsigned long long>(__ldcg(Frp + n_v));
-        const unsigned long long nout = static_cast<unsigned long long>(__ldcg(out.rowptr + n_v));
         st->skeleton_total = ld_relaxed(&st->skeleton_total) + ld_relaxed(&st->skeleton_step);
-        st->nnz_io_total = ld_relaxed(&st->nnz_io_total) + nin + nout;
+        st->nnz_io_total = ld_relaxed(&st->nnz_io_total) + ld_relaxed(&st->nnz_io_step);
+        st->nnz = ld_relaxed(&st->nnz_step);
         st->epoch = epoch + 1u;
       }
       st->skeleton_step = 0ull;
-      st->ticket = 0u;
+      st->nnz_io_step = 0ull;
+      st->nnz_step = 0ull;
       st->done = 0u;
       __threadfence();
     }
@@ -355,24 +526,27 @@ __global__ void __launch_bounds__(B) step_kernel_impl(const JobDesc* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// seeding, labels, conversions
+// seeding, labels, relayout, conversions
 // ---------------------------------------------------------------------------
 template <int DT>
 __global__ void seed_fill_kernel(const JobDesc* __restrict__ job, int n_v, int base) {
   using V = Val<DT>;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_v) return;
   const FieldBuf b = job->buf[0];
-  if (i < n_v) {
-    b.rowptr[i] = i;
-    b.ids[i] = static_cast<uint16_t>(base);
-    static_cast<typename V::T*>(b.vals)[i] = V::round(1.0f);
-  }
-  if (i == 0) b.rowptr[n_v] = n_v;
+  const int tile = i / kTile;
+  const int off = tile * job->tile_cap + (i - tile * kTile);
+  b.rows[i] = make_int2(off, 1);
+  b.ids[off] = static_cast<uint16_t>(base);
+  static_cast<typename V::T*>(b.vals)[off] = V::round(1.0f);
 }
 
 __global__ void seed_scatter_kernel(const JobDesc* __restrict__ job, int k, const int32_t* __restrict__ seeds) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < k) job->buf[0].ids[seeds[s]] = static_cast<uint16_t>(s);
+  if (s >= k) return;
+  const int v = seeds[s];
+  const int tile = v / kTile;
+  job->buf[0].ids[tile * job->tile_cap + (v - tile * kTile)] = static_cast<uint16_t>(s);
 }
 
 template <int DT>
@@ -384,16 +558,33 @@ __global__ void labels_kernel(const JobDesc* __restrict__ job, int n_v, int32_t*
   const uint32_t epoch = job->st->epoch;
   const FieldBuf b = job->buf[epoch & 1u];
   const int base = job->n_layers - 1;
-  const int p0 = b.rowptr[i], p1 = b.rowptr[i + 1];
+  const int2 r = b.rows[i];
   int best = -1;
   float bv = -1.0f;
   const typename V::T* vals = static_cast<const typename V::T*>(b.vals);
-  for (int p = p0; p < p1; ++p) {     // ids ascending: strict > keeps the lowest id on a tie
+  for (int p = r.x; p < r.x + r.y; ++p) {   // ids ascending: strict > keeps the lowest id on a tie
     const float v = V::widen(vals[p]);
     if (v > bv) { bv = v; best = b.ids[p]; }
   }
   labels[i] = (best == base) ? -1 : best;
   if (maxval) maxval[i] = bv;
+}
+
+template <int DT>
+__global__ void relayout_kernel(const int2* __restrict__ rows_from, const uint16_t* __restrict__ ids_from,
+                                const void* __restrict__ vals_from, int cap_from, int2* __restrict__ rows_to,
+                                uint16_t* __restrict__ ids_to, void* __restrict__ vals_to, int cap_to, int n_v) {
+  using T = typename Val<DT>::T;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_v) return;
+  const int tile = i / kTile;
+  const int2 r = rows_from[i];
+  const int start = r.x - tile * cap_from + tile * cap_to;
+  rows_to[i] = make_int2(start, r.y);
+  for (int p = 0; p < r.y; ++p) {
+    ids_to[start + p] = ids_from[r.x + p];
+    static_cast<T*>(vals_to)[start + p] = static_cast<const T*>(vals_from)[r.x + p];
+  }
 }
 
 template <int DT>
@@ -410,56 +601,40 @@ __global__ void narrow_kernel(const float* __restrict__ src, void* __restrict__ 
   if (i < n) static_cast<typename V::T*>(dst)[i] = V::round(src[i]);
 }
 
-template <int DT, int TIER>
-constexpr auto step_fn() {
-  return &step_kernel_impl<DT, (TIER == 0 ? 16 : TIER == 1 ? 48 : 160), (TIER == 0 ? 256 : TIER == 1 ? 128 : 32)>;
-}
-
 using StepFn = void (*)(const JobDesc*);
-const StepFn kStepFns[3][kNumTiers] = {
-    {step_fn<0, 0>(), step_fn<0, 1>(), step_fn<0, 2>()},
-    {step_fn<1, 0>(), step_fn<1, 1>(), step_fn<1, 2>()},
-    {step_fn<2, 0>(), step_fn<2, 1>(), step_fn<2, 2>()},
-};
-
-size_t tier_smem(int tier) {
-  const StepTier& s = kTiers[tier];
-  return static_cast<size_t>(s.map_slots) * s.block * (4 + 4 + 2);
-}
+const StepFn kStepFns[3] = {&step_kernel_impl<0>, &step_kernel_impl<1>, &step_kernel_impl<2>};
 
 }  // namespace
 
-const void* step_kernel(int dtype, int tier, size_t* smem_bytes) {
-  if (smem_bytes) *smem_bytes = tier_smem(tier);
-  return reinterpret_cast<const void*>(kStepFns[dtype][tier]);
+int step_slots() { return kSlots; }
+
+const void* step_kernel(int dtype) { return reinterpret_cast<const void*>(kStepFns[dtype]); }
+
+cudaError_t launch_step(const JobDesc* d_job, int num_tiles, int dtype, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(num_tiles));
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kStepFns[dtype], d_job);
 }
 
-cudaError_t init_kernels() {
-  for (int d = 0; d < 3; ++d)
-    for (int t = 0; t < kNumTiers; ++t) {
-      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kStepFns[d][t]),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(tier_smem(t)));
-      if (e != cudaSuccess) return e;
-    }
-  return cudaSuccess;
-}
-
-cudaError_t launch_step(const JobDesc* d_job, int num_tiles, int dtype, int tier, cudaStream_t s) {
-  const size_t smem = tier_smem(tier);
-  kStepFns[dtype][tier]<<<num_tiles, kTiers[tier].block, smem, s>>>(d_job);
-  return cudaGetLastError();
-}
+#define LF_DISPATCH(dtype, KERNEL, GRID, BLOCK, STREAM, ...)                       \
+  switch (dtype) {                                                                \
+    case 0: KERNEL<0><<<(GRID), (BLOCK), 0, (STREAM)>>>(__VA_ARGS__); break;        \
+    case 1: KERNEL<1><<<(GRID), (BLOCK), 0, (STREAM)>>>(__VA_ARGS__); break;        \
+    default: KERNEL<2><<<(GRID), (BLOCK), 0, (STREAM)>>>(__VA_ARGS__); break;       \
+  }
 
 cudaError_t launch_seed(const JobDesc* d_job, int n_v, int k, const int32_t* d_seeds, int dtype,
                         cudaStream_t s) {
   const int blocks = (n_v + 255) / 256;
-  const int base = k;
-  switch (dtype) {
-    case 0: seed_fill_kernel<0><<<blocks, 256, 0, s>>>(d_job, n_v, base); break;
-    case 1: seed_fill_kernel<1><<<blocks, 256, 0, s>>>(d_job, n_v, base); break;
-    default: seed_fill_kernel<2><<<blocks, 256, 0, s>>>(d_job, n_v, base); break;
-  }
+  LF_DISPATCH(dtype, seed_fill_kernel, blocks, 256, s, d_job, n_v, k);
   seed_scatter_kernel<<<(k + 255) / 256, 256, 0, s>>>(d_job, k, d_seeds);
   return cudaGetLastError();
 }
@@ -467,33 +642,30 @@ cudaError_t launch_seed(const JobDesc* d_job, int n_v, int k, const int32_t* d_s
 cudaError_t launch_labels(const JobDesc* d_job, int n_v, int dtype, int32_t* d_labels, float* d_maxval,
                           cudaStream_t s) {
   const int blocks = (n_v + 255) / 256;
-  switch (dtype) {
-    case 0: labels_kernel<0><<<blocks, 256, 0, s>>>(d_job, n_v, d_labels, d_maxval); break;
-    case 1: labels_kernel<1><<<blocks, 256, 0, s>>>(d_job, n_v, d_labels, d_maxval); break;
-    default: labels_kernel<2><<<blocks, 256, 0, s>>>(d_job, n_v, d_labels, d_maxval); break;
-  }
+  LF_DISPATCH(dtype, labels_kernel, blocks, 256, s, d_job, n_v, d_labels, d_maxval);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relayout(const int2* rows_from, const uint16_t* ids_from, const void* vals_from,
+                            int cap_from, int2* rows_to, uint16_t* ids_to, void* vals_to, int cap_to,
+                            int n_v, int dtype, cudaStream_t s) {
+  const int blocks = (n_v + 255) / 256;
+  LF_DISPATCH(dtype, relayout_kernel, blocks, 256, s, rows_from, ids_from, vals_from, cap_from, rows_to,
+              ids_to, vals_to, cap_to, n_v);
   return cudaGetLastError();
 }
 
 cudaError_t launch_widen(const void* src, float* dst, int64_t n, int dtype, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-  switch (dtype) {
-    case 0: widen_kernel<0><<<blocks, 256, 0, s>>>(src, dst, n); break;
-    case 1: widen_kernel<1><<<blocks, 256, 0, s>>>(src, dst, n); break;
-    default: widen_kernel<2><<<blocks, 256, 0, s>>>(src, dst, n); break;
-  }
+  LF_DISPATCH(dtype, widen_kernel, blocks, 256, s, src, dst, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_narrow(const float* src, void* dst, int64_t n, int dtype, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-  switch (dtype) {
-    case 0: narrow_kernel<0><<<blocks, 256, 0, s>>>(src, dst, n); break;
-    case 1: narrow_kernel<1><<<blocks, 256, 0, s>>>(src, dst, n); break;
-    default: narrow_kernel<2><<<blocks, 256, 0, s>>>(src, dst, n); break;
-  }
+  LF_DISPATCH(dtype, narrow_kernel, blocks, 256, s, src, dst, n);
   return cudaGetLastError();
 }
 

@@ -48,7 +48,7 @@ def single_step_parity(lf, oracle, m, seeds, checks, params=None):
             skg = mesh.stats()["skeleton_total"] - sk0
             Fg = field_from_lib(*mesh.get_field(), F.n_layers, oracle)
             amb = ambiguous_rows(mg)
-            r = compare(Fo, Fg, amb)
+            r = compare(Fo, Fg, amb, oracle)
             r.update(t=t, sk_diff=abs(int(skg) - int(sko)))
             out.append(r)
         if t < last:
@@ -57,12 +57,15 @@ def single_step_parity(lf, oracle, m, seeds, checks, params=None):
     return out
 
 
-def check_results(res, max_tie_frac=0.01):
+def check_results(res, max_disagree_frac=0.05):
+    """Every row agrees within FIELD_TOL with an identical pattern, except
+    rows whose decisions are ties; those stay a small fraction."""
     for r in res:
+        assert r["unexplained"] == 0, r
         assert r["max_err"] <= FIELD_TOL, r
         assert r["pattern_mismatch"] == 0, r
-        assert r["tie_rows"] <= max_tie_frac * r["rows"], r
-        assert r["sk_diff"] <= 2 * r["tie_rows"], r
+        assert r["disagreeing_rows"] <= max_disagree_frac * r["rows"] + 2, r
+        assert r["sk_diff"] <= 16 * r["disagreeing_rows"], r
 
 
 @pytest.mark.parametrize("name", list(MESHES))
@@ -81,7 +84,7 @@ def test_single_step_parity(lf, oracle_mod, name):
 def test_single_step_parity_other_coefficients(lf, oracle_mod, params):
     m = synth.planar_grid(40, seed=8)
     res = single_step_parity(lf, oracle_mod, m, synth.sample_seeds(m.n_v, 30, 4), set(range(0, 60, 3)), params)
-    check_results(res, max_tie_frac=0.02)
+    check_results(res)
 
 
 def test_trajectory_icosphere_300_steps(lf, oracle_mod):
@@ -181,36 +184,27 @@ def random_field(n_v, n_layers, per_row, rng):
     return np.array(rp, np.int64), np.array(ids, np.int32), np.array(vals, np.float32)
 
 
-def test_map_tiers_escalate_and_match(lf, oracle_mod):
-    m = synth.planar_grid(20, seed=6)
-    rng = np.random.default_rng(5)
-    for per_row, n_layers, want_slots in [(5, 200, 48), (14, 400, 160)]:
-        rp, ids, vals = random_field(m.n_v, n_layers, per_row, rng)
-        mesh = lf.Mesh(m.V, m.F)
-        mesh.set_field(rp, ids, vals, n_layers)
-        mesh.step(1)
-        st = mesh.stats()
-        assert st["map_slots"] == want_slots and st["retries"] >= 1
-        L = oracle_mod.cotan_laplacian(m.V, m.F)
-        Fin = oracle_mod.Field(rp, ids, vals.astype(np.float64), n_layers)
-        Fo, _, mg = oracle_mod.step(L, Fin, margins=True)
-        Fg = field_from_lib(*mesh.get_field(), n_layers, oracle_mod)
-        r = compare(Fo, Fg, ambiguous_rows(mg))
-        assert r["max_err"] <= FIELD_TOL and r["pattern_mismatch"] == 0, r
-        mesh.close()
-
-
-def test_map_overflow_beyond_last_tier_is_an_error(lf):
-    m = synth.planar_grid(12, seed=6)
-    rp, ids, vals = random_field(m.n_v, 4000, 40, np.random.default_rng(2))
+@pytest.mark.parametrize("per_row,n_layers", [(2, 50), (5, 200), (14, 400), (40, 4000)])
+def test_large_layer_unions_match(lf, oracle_mod, per_row, n_layers):
+    """Neighbourhoods holding up to a few hundred layers: beyond its register
+    slots the kernel enumerates the union itself (no re-run for the union;
+    the output may still outgrow a tile segment, which is re-run after
+    growth)."""
+    m = synth.planar_grid(16 if per_row > 20 else 20, seed=6)
+    rng = np.random.default_rng(per_row)
+    rp, ids, vals = random_field(m.n_v, n_layers, per_row, rng)
     mesh = lf.Mesh(m.V, m.F)
-    mesh.set_field(rp, ids, vals, 4000)
-    with pytest.raises(lf.LFError) as ei:
-        mesh.step(1)
-    assert ei.value.status == lf.LF_ERR_CAPACITY
-    # the handle stays usable and the field is unchanged
-    rp2, ids2, vals2 = mesh.get_field()
-    assert np.array_equal(rp2, rp) and np.array_equal(ids2, ids) and np.array_equal(vals2, vals)
+    mesh.set_field(rp, ids, vals, n_layers)
+    mesh.step(1)
+    st = mesh.stats()
+    assert st["map_slots"] == 6
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    Fin = oracle_mod.Field(rp, ids, vals.astype(np.float64), n_layers)
+    Fo, _, mg = oracle_mod.step(L, Fin, margins=True)
+    Fg = field_from_lib(*mesh.get_field(), n_layers, oracle_mod)
+    r = compare(Fo, Fg, ambiguous_rows(mg), oracle_mod)
+    assert r["unexplained"] == 0 and r["max_err"] <= FIELD_TOL, r
+    mesh.close()
 
 
 def test_checkpoint_resume_is_bit_exact(lf):
@@ -265,7 +259,7 @@ def test_single_seed_and_tiny_mesh(lf, oracle_mod):
     F = np.array([[0, 1, 2]], np.int32)
     tri = synth.Mesh(V, F)
     res = single_step_parity(lf, oracle_mod, tri, np.array([1], np.int32), set(range(12)))
-    check_results(res, max_tie_frac=1.0)
+    check_results(res)
     m = synth.icosphere(2)
     res = single_step_parity(lf, oracle_mod, m, np.array([17], np.int32), set(range(0, 30)))
     check_results(res)
