@@ -273,8 +273,9 @@ int64_t orc_lt(int64_t n_v, int32_t n_layers,
  *   discrete decisions are from flipping under rounding:
  *   [0] min over the entries of G with F(i,l) = 0 of |G_il| / sum_j |L_ij F_jl|
  *       (the irows test),
- *   [1] min over irows of |F_j + d dt| / (|F_j| + dt sum of |terms of d|)
- *       (the clamp to zero),
+ *   [1] min over irows of |F_j + d dt| / (|F_j| + dt sum of |terms of d|),
+ *       each G_l in those terms counted as sum_j |L_ij F_jl| since G_l is
+ *       itself a cancelling sum (the clamp to zero),
  *   [2] n_i.  HUGE_VAL where there is no such entry.
  */
 int64_t orc_step(int64_t n_v, int32_t n_layers,
@@ -296,7 +297,8 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
   int32_t* S = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_layers);
   double* SF = (double*)malloc(sizeof(double) * (size_t)n_layers);
   double* SG = (double*)malloc(sizeof(double) * (size_t)n_layers);
-  if (!Grp || !Hrp || !S || !SF || !SG) { ret = ORC_ERR_NOMEM; goto done; }
+  double* SGa = (double*)malloc(sizeof(double) * (size_t)n_layers);
+  if (!Grp || !Hrp || !S || !SF || !SG || !SGa) { ret = ORC_ERR_NOMEM; goto done; }
 
   /* (1) L_t */
   for (;;) {
@@ -334,7 +336,7 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
       if (lg == l) ++pg;
       if (fv == 0.0 && ga > 0.0 && fabs(gv) / ga < mG) mG = fabs(gv) / ga;
       if (fv > 0.0 || (fv == 0.0 && gv > 0.0)) {
-        S[n] = l; SF[n] = fv; SG[n] = gv; ++n;
+        S[n] = l; SF[n] = fv; SG[n] = gv; SGa[n] = ga; ++n;
       }
     }
     skel += n;
@@ -347,10 +349,10 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
         double sum = 0.0, sabs = 0.0;
         for (int32_t ll = 0; ll < n; ++ll) {
           int32_t l = S[ll];
-          double ta = 0.5 * (coef_sym(Am, c.a_cc, c.a_cb, n_layers, j, l) - coef_sym(Am, c.a_cc, c.a_cb, n_layers, kx, l)) * SG[ll];
+          double ca = 0.5 * (coef_sym(Am, c.a_cc, c.a_cb, n_layers, j, l) - coef_sym(Am, c.a_cc, c.a_cb, n_layers, kx, l));
           double tw = (coef_sym(Wm, c.w_cc, c.w_cb, n_layers, j, l) - coef_sym(Wm, c.w_cc, c.w_cb, n_layers, kx, l)) * SF[ll];
-          sum += ta + tw;
-          sabs += fabs(ta) + fabs(tw);
+          sum += ca * SG[ll] + tw;
+          sabs += fabs(ca) * SGa[ll] + fabs(tw);
         }
         double te = coef_e(Em, &c, n_layers, j, kx) * sqrt(SF[jj] * SF[kk]);
         d += -(c.mu / n) * (sum - te);
@@ -398,7 +400,7 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
 
 done:
   free(Grp); free(Gid); free(Gval); free(Gab); free(Hrp); free(Hid); free(Hval);
-  free(S); free(SF); free(SG);
+  free(S); free(SF); free(SG); free(SGa);
   return ret;
 }
 
