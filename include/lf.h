@@ -207,8 +207,54 @@ void lf_destroy_mesh(lf_mesh m);
 /* Static string for a status code. */
 const char* lf_status_string(lf_status s);
 
-/* Message of the last failed call on m (m = NULL: last failed create). */
+/* Message of the last failed call on m (m = NULL: the last failed call made
+ * without a handle on this thread: lf_create_mesh*, lf_step_noalloc). */
 const char* lf_last_error(lf_mesh m);
+
+/*
+ * One time-iteration for callers that cannot allocate device memory.
+ *
+ * No counterpart in the paper.  Every other entry point here allocates (the
+ * handle's buffers, the job descriptor, the step's status words).  Callers
+ * that own all device memory themselves -- a framework with its own memory
+ * pool, a service that allocates only at start-up, code running where an
+ * allocation is not allowed -- can call this instead: it runs the same step
+ * kernel as lf_step on buffers the caller provides, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The kernel's scratch (its job
+ * descriptor and status counters, 1 KiB) lives in a static device array that
+ * every GPU loading this library holds until the process exits.
+ *
+ * All pointers are device pointers on the current device; the call runs on
+ * cuda_stream (NULL = legacy default stream) and returns when the step is
+ * done.  Layout (FP32 values only):
+ *   d_L_rowptr  n_v + 1 int32: row offsets of the operator, off-diagonal entries
+ *               only (L_ii = -sum_j L_ij is implied);
+ *   d_L_colval  2 int32 per entry: column, then the IEEE-754 bits of L_ij
+ *               (8-byte aligned);
+ *   field in / out, tile-segmented CSR with T = ceil(n_v / 256) tiles: vertex i
+ *   belongs to tile i / 256; d_rows_* hold 2 int32 per vertex (start, count),
+ *   8-byte aligned; the rows of tile t lie one after another, layer ids
+ *   ascending within a row, inside entries [t * tile_cap, (t + 1) * tile_cap)
+ *   of d_ids_* (uint16) and d_vals_* (float); both fields hold T * tile_cap
+ *   entries.  n_layers = k + 1 (the base layer is k).
+ *   nnz_out (host, nullable): entries of the output field.
+ *   need_tile_cap (host, nullable): on LF_ERR_CAPACITY, the tile_cap needed.
+ * Limits: tile_cap a multiple of 16 and >= 256; n_v <= 2^31 - 257;
+ * T * tile_cap <= 2^31 - 1.  Larger sizes are rejected (LF_ERR_INVALID or
+ * LF_ERR_CAPACITY) with a message in lf_last_error(NULL); so is a field_dtype
+ * other than LF_F32.
+ * The first call on a device looks up the scratch's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the scratch and resets it: calls that overlap on
+ * the GPU (other streams, other threads) race and must be serialised by the
+ * caller.
+ */
+lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers,
+                          const int32_t* d_L_rowptr, const int32_t* d_L_colval,
+                          const int32_t* d_rows_in, const uint16_t* d_ids_in, const float* d_vals_in,
+                          int32_t* d_rows_out, uint16_t* d_ids_out, float* d_vals_out,
+                          int32_t tile_cap, const lf_params* params,
+                          int64_t* nnz_out, int64_t* need_tile_cap);
 
 #ifdef __cplusplus
 }

@@ -83,9 +83,13 @@ _lib.lf_status_string.argtypes = [ctypes.c_int]
 _lib.lf_status_string.restype = ctypes.c_char_p
 _lib.lf_last_error.argtypes = [_P]
 _lib.lf_last_error.restype = ctypes.c_char_p
+_lib.lf_step_noalloc.argtypes = [_P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _i32, ctypes.POINTER(lf_params),
+                                 ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+_lib.lf_step_noalloc.restype = ctypes.c_int
 
 EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_step", "lf_labels",
-            "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error"]
+            "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
+            "lf_step_noalloc"]
 
 
 class LFError(RuntimeError):
@@ -203,6 +207,24 @@ def lf_stats(mesh):
 
 def lf_destroy_mesh(mesh):
     _lib.lf_destroy_mesh(mesh)
+
+
+def lf_step_noalloc(stream, n_v, n_layers, L_rowptr, L_colval, rows_in, ids_in, vals_in, rows_out, ids_out,
+                    vals_out, tile_cap, params=None):
+    """One step on caller-owned device buffers (integer device addresses).
+
+    Returns (nnz_out, need_tile_cap); raises LFError on failure.
+    """
+    nnz = _i64(0)
+    need = _i64(0)
+    st = _lib.lf_step_noalloc(stream, n_v, n_layers, L_rowptr, L_colval, rows_in, ids_in, vals_in, rows_out,
+                              ids_out, vals_out, tile_cap, ctypes.byref(params) if params is not None else None,
+                              ctypes.byref(nnz), ctypes.byref(need))
+    if st != LF_OK:
+        err = LFError(st, _lib.lf_last_error(None).decode(errors="replace"))
+        err.need_tile_cap = need.value
+        raise err
+    return nnz.value, need.value
 
 
 def lf_status_string(status):

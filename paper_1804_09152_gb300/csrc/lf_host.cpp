@@ -380,6 +380,10 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
 
 }  // namespace
 
+namespace lf {
+void set_last_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace lf
+
 extern "C" {
 
 void lf_default_params(lf_params* p) {

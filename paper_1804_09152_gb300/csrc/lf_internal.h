@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace lf {
 
 // Error bits raised on the device (DevStatus::err).
@@ -81,5 +83,8 @@ cudaError_t launch_widen(const void* src, float* dst, int64_t n, int dtype, cuda
 cudaError_t launch_narrow(const float* src, void* dst, int64_t n, int dtype, cudaStream_t s);
 
 inline int value_bytes(int dtype) { return dtype == 0 ? 4 : 2; }
+
+// Message returned by lf_last_error(NULL) (thread-local).
+void set_last_error(const std::string& msg);
 
 }  // namespace lf
