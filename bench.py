@@ -293,17 +293,195 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def _job_bytes(st, n_v):
+    """Algorithmic bytes of one step of one job, without the field traffic."""
+    return 4 * (n_v + 1) + 8 * st["operator_nnz"] + 2 * 4 * (n_v + 1)
+
+
+def run_batch(args):
+    """Batching form: 64 mixed jobs (icosphere / noisy torus, 10k-600k vertices,
+    32-2048 seeds, FP32 / BF16) advanced together by lf_step_batch, against the
+    same jobs stepped one at a time with lf_step."""
+    import torch
+    import paper_1804_09152_gb300 as pkg
+    pkg.build()
+    from paper_1804_09152_gb300 import _lib as lf
+
+    specs = synth.batch_mix()
+    T = specs[0].steps
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    cache = {}
+    meshes, seeds, geo = [], [], []
+    with torch.cuda.stream(stream):
+        dev = lf.torch_device(stream)
+        for sp in specs:
+            key = (sp.kind, sp.size)
+            if key not in cache:
+                cache[key] = synth.make_mesh(sp)
+            m = cache[key]
+            geo.append(m)
+            meshes.append(lf.Mesh(m.V, m.F, device=dev, field_dtype=sp.dtype))
+            seeds.append(synth.sample_seeds(m.n_v, min(sp.k, m.n_v // 4), sp.seed_stream))
+
+        def seed_all():
+            for mesh, sd in zip(meshes, seeds):
+                mesh.seed(sd)
+
+        def timed(fn):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / 1e3
+
+        for _ in range(args.warmup):
+            seed_all()
+            lf.lf_step_batch(meshes, T)
+        times, units, io = [], 0, 0
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for _ in range(args.steps):
+                seed_all()
+                times.append(timed(lambda: lf.lf_step_batch(meshes, T)))
+                sts = [mesh.stats() for mesh in meshes]
+                units += sum(s["skeleton_total"] for s in sts)
+                io += sum(s["nnz_io_total"] * (2 + s["value_bytes"]) for s in sts)
+        # the same jobs one at a time
+        seed_all()
+        t_plain = timed(lambda: [mesh.step(T) for mesh in meshes])
+        units_plain = sum(mesh.stats()["skeleton_total"] for mesh in meshes)
+        # end to end from host buffers: create, seed, batch, labels, destroy
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fresh = [lf.Mesh(m.V, m.F, device=dev, field_dtype=sp.dtype) for m, sp in zip(geo, specs)]
+        for mesh, sd in zip(fresh, seeds):
+            mesh.seed(sd)
+        lf.lf_step_batch(fresh, T)
+        e2e_units = 0
+        for mesh in fresh:
+            mesh.labels()
+            e2e_units += mesh.stats()["skeleton_total"]
+            mesh.close()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        sts = [mesh.stats() for mesh in meshes]
+    secs = sum(times)
+    value = units / secs
+    bytes_step = sum(_job_bytes(s, m.n_v) for s, m in zip(sts, geo))
+    achieved = (args.steps * T * bytes_step + io) / secs / 1e9
+    peak, peak_kind = measured_peaks()
+    n_v_total = sum(m.n_v for m in geo)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+bf16", "data": "synthetic",
+        "config": {"workload": "batch64", "jobs": len(specs), "n_v_total": n_v_total,
+                   "time_steps_per_job": T, "bf16_jobs": sum(sp.dtype == "bf16" for sp in specs),
+                   "desc": "64 jobs: icosphere level 4-8 or noisy torus (p=1/2), n_v log-uniform 10k-600k, "
+                           "k log-uniform 32-2048, FP32 or BF16 (p=1/2), 1000 steps (stream 6)",
+                   "l2": "flushed before every timed batch (512 MiB write); the batch working set exceeds L2"},
+        "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": value / (units_plain / t_plain),
+                     "desc": "the same jobs stepped one after another with lf_step"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind},
+        "e2e": {"value": e2e_units / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(4 * (m.n_v + 1) + 8 * s["operator_nnz"] for s, m in zip(sts, geo))),
+                "d2h_bytes_per_step": int(4 * n_v_total), "jobs": len(specs)},
+        "gpu_launches": args.steps * T * 2,
+        "clocks": clk.summary(),
+    }
+    for mesh in meshes:
+        mesh.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Serving form: a prefix of the Poisson trace (200 jobs/s; n_v log-normal
+    in [5k, 2M]; icosphere / torus / grid; 16-8192 seeds; 500-3000 steps)
+    submitted at its arrival times to an lf_server with a 150 GB budget."""
+    import torch
+    import paper_1804_09152_gb300 as pkg
+    pkg.build()
+    from paper_1804_09152_gb300 import _lib as lf
+
+    trace = synth.serve_trace()[: args.serve_jobs]
+    cache = {}
+    for sp in trace:
+        if (sp.kind, sp.size) not in cache:
+            cache[(sp.kind, sp.size)] = synth.make_mesh(sp)
+    seeds = [synth.sample_seeds(cache[(sp.kind, sp.size)].n_v, sp.k, sp.seed_stream) for sp in trace]
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        with lf.Server() as srv:
+            t0 = time.monotonic_ns()
+            ids = []
+            for sp, sd in zip(trace, seeds):
+                due = t0 + int(sp.arrival * 1e9)
+                while time.monotonic_ns() < due:
+                    time.sleep(min(1e-3, max(0.0, (due - time.monotonic_ns()) / 1e9)))
+                m = cache[(sp.kind, sp.size)]
+                ids.append((srv.submit(m.V, m.F, sd, sp.steps, arrival_ns=due), m.n_v))
+            assert srv.drain(3600.0) == lf.LF_OK
+            t_end = time.monotonic_ns()
+            lat, units = [], 0
+            for jid, n_v in ids:
+                st, info, _ = srv.wait(jid, 0.0, release=True)
+                assert st == lf.LF_OK, st
+                lat.append((info["finish_ns"] - info["arrival_ns"]) / 1e6)
+                units += info["skeleton_total"]
+            sst = srv.stats()
+    wall = (t_end - t0) / 1e9
+    # the same jobs one at a time through lf_step (no arrivals: back to back)
+    t1 = time.perf_counter()
+    units_plain = 0
+    for sp, sd in zip(trace, seeds):
+        m = cache[(sp.kind, sp.size)]
+        with lf.Mesh(m.V, m.F) as mesh:
+            mesh.seed(sd)
+            mesh.step(sp.steps)
+            mesh.labels()
+            units_plain += mesh.stats()["skeleton_total"]
+    t_plain = time.perf_counter() - t1
+    line = {
+        "metric": METRIC, "value": units / wall, "unit": UNIT, "n_gpus": 1, "steps": len(trace), "warmup": 0,
+        "ms_per_step": 1e3 * wall / len(trace), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve", "jobs": len(trace), "arrival_rate_per_s": 200.0,
+                   "last_arrival_s": trace[-1].arrival, "hbm_budget_bytes": 150_000_000_000,
+                   "desc": "first jobs of the Poisson trace (stream 7): n_v log-normal in [5k, 2M], icosphere / "
+                           "torus / grid, k log-uniform 16-8192, steps U{500..3000}; a step of this line is one job"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "jobs_per_s": len(trace) / wall,
+        "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": (units / wall) / (units_plain / t_plain),
+                     "desc": "the same jobs back to back, one at a time, lf_create_mesh to lf_labels"},
+        "server": {"peak_running": sst["peak_running"], "peak_bytes": sst["peak_bytes"], "batches": sst["batches"],
+                   "busy_s": sst["busy_ns"] / 1e9},
+        "e2e": {"value": units / wall, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="grid512")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch64", "serve"], default="grid512")
+    ap.add_argument("--serve-jobs", type=int, default=100)
     ap.add_argument("--cpu-sample-steps", type=int, default=200)
     ap.add_argument("--ref-sample-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload == "batch64":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

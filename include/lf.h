@@ -171,6 +171,24 @@ lf_status lf_seed(lf_mesh m, const int32_t* seed_vertices, int32_t k);
 lf_status lf_step(lf_mesh m, int32_t n_iters);
 
 /*
+ * Batching form: meshes[a] advances by n_iters[a] time-iterations (as
+ * lf_step), for 1 <= n <= 64 meshes, all in shared launches: each step is one
+ * kernel launch per storage type present whose CTAs cover the tiles of every
+ * mesh of that type, and runs of 128 steps are replayed as one CUDA graph
+ * (one independent chain per storage type).  A mesh leaves the launches when
+ * its count is reached.  Results are bit-identical to lf_step on each mesh
+ * alone.  The batch runs on meshes[0]'s stream after every mesh's earlier work
+ * has finished and returns when all steps are done.  A mesh whose field
+ * outgrows its buffers is grown and its step re-run while the others go on.
+ * meshes and n_iters are caller-owned arrays of n entries, read during the
+ * call.  Errors: LF_ERR_INVALID for n outside [1, 64], a null array, a
+ * negative count or a repeated mesh; LF_ERR_STATE for an unseeded mesh, or a
+ * vertex that sums to zero (that mesh stops where it failed, the others
+ * finish); LF_ERR_OOM, LF_ERR_CUDA.
+ */
+lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters);
+
+/*
  * Sharp labels (Sec. 6: the field of largest value at each vertex).
  * labels[i] = layer of the largest value at vertex i, the lowest layer id on
  * a tie, and -1 when that layer is the base layer.  labels: n_v int32.
@@ -215,14 +233,14 @@ const char* lf_last_error(lf_mesh m);
  * One time-iteration for callers that cannot allocate device memory.
  *
  * No counterpart in the paper.  Every other entry point here allocates (the
- * handle's buffers, the job descriptor, the step's status words).  Callers
+ * handle's buffers and the step's status words).  Callers
  * that own all device memory themselves -- a framework with its own memory
  * pool, a service that allocates only at start-up, code running where an
  * allocation is not allowed -- can call this instead: it runs the same step
  * kernel as lf_step on buffers the caller provides, and calls no cudaMalloc,
- * cudaFree or other allocating routine.  The kernel's scratch (its job
- * descriptor and status counters, 1 KiB) lives in a static device array that
- * every GPU loading this library holds until the process exits.
+ * cudaFree or other allocating routine.  The kernel's scratch (its status and
+ * counter words; 1 KiB reserved) lives in a static device array that every
+ * GPU loading this library holds until the process exits.
  *
  * All pointers are device pointers on the current device; the call runs on
  * cuda_stream (NULL = legacy default stream) and returns when the step is
@@ -255,6 +273,114 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers,
                           int32_t* d_rows_out, uint16_t* d_ids_out, float* d_vals_out,
                           int32_t tile_cap, const lf_params* params,
                           int64_t* nnz_out, int64_t* need_tile_cap);
+
+/*
+ * Lloyd-like iterations (Sec. 5): `rounds` times, new seeds from the current
+ * field, a fresh field from them (as lf_seed) and steps_per_round steps (as
+ * lf_step).  A cell is the set of vertices with an entry of its layer; its
+ * centre of mass is the area-weighted mean of the barycentres of the faces
+ * with at least one cell vertex, and the line through it along the area-
+ * weighted mean normal of those faces is intersected with them (both
+ * directions; the hit nearest to the centre wins, ties to the lowest face
+ * id).  The new seed is the vertex of the hit face nearest to the hit point
+ * (ties to the lowest vertex id); a miss, or a zero mean normal, keeps the
+ * seed.  When several cells pick one vertex, the cell whose old seed it is
+ * keeps it, else the lowest cell id, and the others return to their old
+ * seeds (repeated until the seeds are distinct).  Geometry is FP64 on the
+ * device; the per-cell sums are FP64 atomics.  seeds_out (nullable) gets the
+ * k final seed vertices.  rounds = 0 only reports the seeds.  Needs a mesh
+ * made by lf_create_mesh (the geometry) whose field came from lf_seed (or
+ * lf_set_field with the same k after lf_seed): else LF_ERR_STATE.  Errors:
+ * LF_ERR_INVALID (negative counts), LF_ERR_OOM, LF_ERR_CUDA, and those of
+ * lf_step.
+ */
+lf_status lf_lloyd(lf_mesh m, int32_t rounds, int32_t steps_per_round, int32_t* seeds_out);
+
+/* ------------------------------------------------------------------------
+ * Serving form: continuous batching of tessellation jobs.
+ *
+ * A server owns one CUDA stream and one scheduler thread.  lf_server_submit
+ * validates a job (mesh, seeds, step count, parameters), builds its cotangent
+ * operator on the calling thread and queues it; nothing is put on the device
+ * yet.  The scheduler admits queued jobs in arrival order while fewer than
+ * max_active jobs run and the estimated device bytes of the admitted jobs
+ * stay within hbm_budget_bytes (a job larger than the whole budget fails with
+ * LF_ERR_OOM), creates and seeds each one (lf_create_mesh, lf_seed), and
+ * advances all running jobs together with lf_step_batch in chunks of
+ * chunk_steps.  A job that has taken its n_iters steps gets its sharp labels
+ * (Sec. 6) copied to the host and its device memory freed; admission then
+ * runs again.  A job that fails (e.g. a vertex summing to zero) is retired
+ * with its status; the others continue.  The paper runs one mesh at a time;
+ * this runtime has no counterpart there.
+ * ------------------------------------------------------------------------ */
+typedef struct lf_server_s* lf_server;
+
+typedef struct {
+  int64_t hbm_budget_bytes;  /* device bytes the running jobs may hold (default 150e9)   */
+  int32_t max_active;        /* jobs advanced together, 1..64 (default 64)               */
+  int32_t chunk_steps;       /* steps between admission rounds, >= 1 (default 256)      */
+} lf_server_params;
+
+typedef enum { LF_JOB_QUEUED = 0, LF_JOB_RUNNING = 1, LF_JOB_DONE = 2, LF_JOB_FAILED = 3 } lf_job_state;
+
+typedef struct {
+  int32_t state;             /* lf_job_state                                             */
+  int32_t status;            /* LF_OK, or the lf_status a failed job ended with         */
+  int64_t n_v;
+  int64_t steps;             /* n_iters of the job                                       */
+  int64_t steps_done;
+  int64_t arrival_ns;        /* CLOCK_MONOTONIC, as given to lf_server_submit            */
+  int64_t admit_ns;          /* when the scheduler put the job on the device (0: not yet) */
+  int64_t finish_ns;         /* when its labels were on the host (0: not yet)            */
+  uint64_t skeleton_total;   /* nnz-updates of the job                                   */
+  int64_t device_bytes;      /* device bytes the job held at the end                     */
+} lf_job_info;
+
+typedef struct {
+  int64_t submitted, done, failed, queued, running;
+  int64_t bytes_in_use, peak_bytes;   /* device bytes of the running jobs                */
+  int64_t peak_running;
+  int64_t batches;                    /* lf_step_batch calls made                        */
+  int64_t busy_ns;                    /* scheduler time spent with running jobs          */
+  uint64_t skeleton_total;            /* nnz-updates of the finished jobs                */
+} lf_server_stats_t;
+
+void lf_server_default_params(lf_server_params* p);
+
+/* Creates a server on the current CUDA device.  dev may be NULL; its
+ * cuda_stream is ignored (the server makes its own) and its allocation hooks
+ * are used from the scheduler thread when set.  Errors: LF_ERR_INVALID (bad
+ * parameters), LF_ERR_CUDA (no device, stream creation). */
+lf_status lf_server_create(const lf_device* dev, const lf_server_params* sp, lf_server* out);
+
+/* Queues one job.  V (n_v x 3 doubles), F (n_f x 3 int32), seeds (k int32),
+ * params (NULL: defaults) are caller-owned and copied before the call returns.
+ * arrival_ns is the job's arrival time on CLOCK_MONOTONIC (0: now); latency is
+ * finish_ns - arrival_ns.  *job_id gets a positive id.  Errors: LF_ERR_INVALID
+ * for any input lf_create_mesh or lf_seed would reject, or n_iters < 0;
+ * LF_ERR_STATE after lf_server_destroy began. */
+lf_status lf_server_submit(lf_server s, const double* V, int64_t n_v, const int32_t* F, int64_t n_f,
+                           const int32_t* seeds, int32_t k, int32_t n_iters, const lf_params* params,
+                           int64_t arrival_ns, int64_t* job_id);
+
+/* Waits up to timeout_s seconds (0: just looks) for the job to finish and
+ * fills *info.  When it is done and labels is not NULL, its n_v labels are
+ * copied there.  With release != 0 a finished job's record is dropped after
+ * the copy (its id becomes unknown).  Returns LF_OK once the job is done,
+ * LF_ERR_TIMEOUT while it is queued or running (info filled), the job's own
+ * status when it failed, LF_ERR_INVALID for an unknown id. */
+lf_status lf_server_wait(lf_server s, int64_t job_id, double timeout_s, lf_job_info* info, int32_t* labels,
+                         int32_t release);
+
+/* Waits up to timeout_s seconds until no job is queued or running.  Returns
+ * LF_OK or LF_ERR_TIMEOUT. */
+lf_status lf_server_drain(lf_server s, double timeout_s);
+
+lf_status lf_server_stats(lf_server s, lf_server_stats_t* out);
+
+/* Stops the scheduler after its current chunk, fails the jobs still queued or
+ * running (LF_ERR_STATE), frees all device memory and the handle. */
+void lf_server_destroy(lf_server s);
 
 #ifdef __cplusplus
 }

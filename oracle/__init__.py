@@ -15,7 +15,8 @@ on Surfaces" (arXiv 1804.09152), cited in the C source:
 * ``step``            -- one time-iteration of Algorithm 1 (Eq. 11-13, Sec. 4),
 * ``step_closed``     -- the same update through its closed form for the
                          class coefficients (cross-check only),
-* ``labels``          -- sharp labels, the layer of largest value (Sec. 6).
+* ``labels``          -- sharp labels, the layer of largest value (Sec. 6),
+* ``lloyd_seeds``     -- one Lloyd-like seed update (Sec. 5), in ``tessellation.py``.
 
 A field is a vertex-major CSR triple ``(rowptr int64[n_v+1], ids int32[nnz],
 vals float64[nnz])``; row i lists the layers present at vertex i with ids

@@ -54,6 +54,32 @@ class lf_stats_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lf_server_params(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("chunk_steps", ctypes.c_int32)]
+
+
+class lf_job_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("n_v", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("steps_done", ctypes.c_int64), ("arrival_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("finish_ns", ctypes.c_int64), ("skeleton_total", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lf_server_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "done", "failed", "queued", "running", "bytes_in_use",
+                                              "peak_bytes", "peak_running", "batches", "busy_ns")] + \
+               [("skeleton_total", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+LF_JOB_QUEUED, LF_JOB_RUNNING, LF_JOB_DONE, LF_JOB_FAILED = range(4)
+
 _P = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
@@ -83,13 +109,33 @@ _lib.lf_status_string.argtypes = [ctypes.c_int]
 _lib.lf_status_string.restype = ctypes.c_char_p
 _lib.lf_last_error.argtypes = [_P]
 _lib.lf_last_error.restype = ctypes.c_char_p
+_lib.lf_step_batch.argtypes = [ctypes.POINTER(_P), _i32, ctypes.POINTER(_i32)]
+_lib.lf_step_batch.restype = ctypes.c_int
 _lib.lf_step_noalloc.argtypes = [_P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _i32, ctypes.POINTER(lf_params),
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
 _lib.lf_step_noalloc.restype = ctypes.c_int
+_lib.lf_lloyd.argtypes = [_P, _i32, _i32, _P]
+_lib.lf_lloyd.restype = ctypes.c_int
+_lib.lf_server_default_params.argtypes = [ctypes.POINTER(lf_server_params)]
+_lib.lf_server_default_params.restype = None
+_lib.lf_server_create.argtypes = [ctypes.POINTER(lf_device), ctypes.POINTER(lf_server_params), ctypes.POINTER(_P)]
+_lib.lf_server_create.restype = ctypes.c_int
+_lib.lf_server_submit.argtypes = [_P, _P, _i64, _P, _i64, _P, _i32, _i32, ctypes.POINTER(lf_params), _i64,
+                                  ctypes.POINTER(_i64)]
+_lib.lf_server_submit.restype = ctypes.c_int
+_lib.lf_server_wait.argtypes = [_P, _i64, ctypes.c_double, ctypes.POINTER(lf_job_info), _P, _i32]
+_lib.lf_server_wait.restype = ctypes.c_int
+_lib.lf_server_drain.argtypes = [_P, ctypes.c_double]
+_lib.lf_server_drain.restype = ctypes.c_int
+_lib.lf_server_stats.argtypes = [_P, ctypes.POINTER(lf_server_stats_t)]
+_lib.lf_server_stats.restype = ctypes.c_int
+_lib.lf_server_destroy.argtypes = [_P]
+_lib.lf_server_destroy.restype = None
 
 EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_step", "lf_labels",
             "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
-            "lf_step_noalloc"]
+            "lf_step_noalloc", "lf_step_batch", "lf_lloyd", "lf_server_default_params", "lf_server_create",
+            "lf_server_submit", "lf_server_wait", "lf_server_drain", "lf_server_stats", "lf_server_destroy"]
 
 
 class LFError(RuntimeError):
@@ -172,6 +218,27 @@ def lf_seed(mesh, seeds):
 
 def lf_step(mesh, n_iters):
     _check(_lib.lf_step(mesh, int(n_iters)), mesh)
+
+
+def lf_step_batch(meshes, n_iters):
+    """Advances meshes[a] by n_iters[a] steps (or every mesh by one int) in shared launches."""
+    arr = (_P * len(meshes))(*[m.h if isinstance(m, Mesh) else m for m in meshes])
+    counts = [int(n_iters)] * len(meshes) if np.isscalar(n_iters) else [int(x) for x in n_iters]
+    if len(counts) != len(meshes):
+        raise ValueError("n_iters needs one count per mesh")
+    cnt = (_i32 * max(1, len(counts)))(*counts)
+    st = _lib.lf_step_batch(arr, len(meshes), cnt)
+    if st != LF_OK:
+        msgs = [_lib.lf_last_error(h).decode(errors="replace") for h in arr if h]
+        msg = next((x for x in msgs if x), "") or _lib.lf_last_error(None).decode(errors="replace")
+        raise LFError(st, msg)
+
+
+def lf_lloyd(mesh, rounds, steps_per_round, k):
+    """Lloyd-like rounds; returns the k seeds afterwards."""
+    out = np.empty(k, np.int32)
+    _check(_lib.lf_lloyd(mesh, int(rounds), int(steps_per_round), _ptr(out)), mesh)
+    return out
 
 
 def lf_labels(mesh, n_v, with_max=False):
@@ -259,6 +326,9 @@ class Mesh:
     def labels(self, with_max=False):
         return lf_labels(self.h, self.n_v, with_max)
 
+    def lloyd(self, rounds, steps_per_round):
+        return lf_lloyd(self.h, rounds, steps_per_round, self.stats()["n_layers"] - 1)
+
     def get_field(self):
         return lf_get_field(self.h, self.n_v)
 
@@ -271,6 +341,96 @@ class Mesh:
     def close(self):
         if self.h:
             lf_destroy_mesh(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lf_server_default_params(**overrides):
+    p = lf_server_params()
+    _lib.lf_server_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def lf_server_create(params=None):
+    out = _P()
+    _check(_lib.lf_server_create(None, ctypes.byref(params) if params is not None else None, ctypes.byref(out)))
+    return out
+
+
+def lf_server_submit(server, V, F, seeds, n_iters, params=None, arrival_ns=0):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    jid = _i64()
+    _check(_lib.lf_server_submit(server, _ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(seeds), seeds.size,
+                                 int(n_iters), ctypes.byref(params) if params is not None else None,
+                                 int(arrival_ns), ctypes.byref(jid)))
+    return jid.value
+
+
+def lf_server_wait(server, job_id, timeout_s=0.0, n_v=None, release=False):
+    """(status, info dict, labels or None); status LF_ERR_TIMEOUT while the job runs."""
+    info = lf_job_info()
+    labels = np.empty(n_v, np.int32) if n_v else None
+    st = _lib.lf_server_wait(server, int(job_id), float(timeout_s), ctypes.byref(info), _ptr(labels),
+                             1 if release else 0)
+    if st == LF_ERR_INVALID:
+        _check(st)
+    return st, info.as_dict(), (labels if st == LF_OK else None)
+
+
+def lf_server_drain(server, timeout_s):
+    return _lib.lf_server_drain(server, float(timeout_s))
+
+
+def lf_server_stats(server):
+    s = lf_server_stats_t()
+    _check(_lib.lf_server_stats(server, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def lf_server_destroy(server):
+    _lib.lf_server_destroy(server)
+
+
+class Server:
+    """Owns one lf_server handle; each method calls the entry point of the same name."""
+
+    def __init__(self, **overrides):
+        self.h = lf_server_create(lf_server_default_params(**overrides))
+
+    def submit(self, V, F, seeds, n_iters, params=None, arrival_ns=0, **overrides):
+        if params is None and overrides:
+            params = lf_default_params(**overrides)
+        return lf_server_submit(self.h, V, F, seeds, n_iters, params, arrival_ns)
+
+    def wait(self, job_id, timeout_s=0.0, n_v=None, release=False):
+        return lf_server_wait(self.h, job_id, timeout_s, n_v, release)
+
+    def drain(self, timeout_s):
+        return lf_server_drain(self.h, timeout_s)
+
+    def stats(self):
+        return lf_server_stats(self.h)
+
+    def close(self):
+        if self.h:
+            lf_server_destroy(self.h)
             self.h = None
 
     def __enter__(self):

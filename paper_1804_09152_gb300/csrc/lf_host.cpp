@@ -51,18 +51,28 @@ struct lf_mesh_s {
   int2* d_Lcv = nullptr;
   lf::FieldBuf buf[2]{};
   lf::DevStatus* d_st = nullptr;
-  lf::JobDesc* d_job = nullptr;
   lf::JobDesc h_job{};
   lf::DevStatus h_st{};
   int32_t* d_labels = nullptr;
   float* d_scratch_f = nullptr;
   int64_t scratch_f_len = 0;
 
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // step graphs by starting parity
+
+  // geometry (lf_create_mesh only) and seeds, for the Lloyd-like update
+  double* d_V = nullptr;         // n_v x 3
+  int32_t* d_tri = nullptr;      // n_f x 3
+  int64_t n_f = 0;
+  std::vector<int32_t> seeds;    // current seed vertex of each cell (empty: unknown)
+  int32_t* d_seed_old = nullptr;
+  int32_t* d_seed_new = nullptr;
+  lf::LloydScratch lloyd{};
+  int64_t lloyd_k = 0;
 
   ~lf_mesh_s() {
     cudaStreamSynchronize(stream);
-    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& g : gexec)
+      if (g) cudaGraphExecDestroy(g);
     for (auto& a : allocs) release(a.p);
   }
 
@@ -192,9 +202,29 @@ bool cotan_rows(int64_t n_v, const double* V, int64_t n_f, const int32_t* F,
   return true;
 }
 
+// The job descriptor travels inside the launch parameters: a change to it
+// only invalidates the captured step graphs.
 lf_status upload_job(lf_mesh m) {
-  LF_CUDA(m, cudaMemcpyAsync(m->d_job, &m->h_job, sizeof(lf::JobDesc), cudaMemcpyHostToDevice, m->stream));
+  for (auto& g : m->gexec) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
   return LF_OK;
+}
+
+// Launch parameters for `steps` steps of this mesh alone, starting from the
+// current buffer.
+lf::BatchParams single_job_params(lf_mesh m, int steps) {
+  lf::BatchParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_jobs = 1;
+  p.step = 0;
+  p.tile_start[0] = 0;
+  p.tile_start[1] = m->num_tiles;
+  p.job[0] = m->h_job;
+  p.job[0].parity0 = static_cast<int32_t>(m->h_st.epoch & 1u);
+  p.job[0].steps = steps;
+  return p;
 }
 
 lf_status upload_status(lf_mesh m) {
@@ -260,41 +290,56 @@ lf_status set_tile_cap(lf_mesh m, int64_t new_cap, bool keep) {
   return upload_job(m);
 }
 
-// A graph of kGraphSteps step launches chained by programmatic edges: each
-// launch may start its CTAs while the previous one drains, and waits inside
+// A graph of independent chains, each of kGraphSteps step launches of one
+// storage type (chain c launches chains[c].second with step = 0, 1, ...).
+// Within a chain each launch is joined to the previous one by a programmatic
+// edge: it may start its CTAs while the previous one drains, and waits inside
 // the kernel (griddepcontrol.wait) before it reads the previous step's output.
-lf_status build_graph(lf_mesh m) {
-  if (m->gexec) return LF_OK;
-  const void* fn = lf::step_kernel(m->dtype);
+cudaError_t make_step_graph(const std::vector<std::pair<int, lf::BatchParams>>& chains, cudaGraphExec_t* out) {
+  *out = nullptr;
   cudaGraph_t g = nullptr;
-  LF_CUDA(m, cudaGraphCreate(&g, 0));
-  void* args[1] = {&m->d_job};
-  cudaKernelNodeParams p{};
-  p.func = const_cast<void*>(fn);
-  p.gridDim = dim3(static_cast<unsigned>(m->num_tiles));
-  p.blockDim = dim3(static_cast<unsigned>(lf::kTile));
-  p.sharedMemBytes = 0;
-  p.kernelParams = args;
-  cudaGraphNode_t prev = nullptr;
-  for (int s = 0; s < kGraphSteps; ++s) {
-    cudaGraphNode_t node = nullptr;
-    cudaError_t e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &p);
-    if (e == cudaSuccess && prev) {
-      cudaGraphEdgeData ed{};
-      ed.from_port = cudaGraphKernelNodePortProgrammatic;
-      ed.to_port = 0;
-      ed.type = cudaGraphDependencyTypeProgrammatic;
-      e = cudaGraphAddDependencies(g, &prev, &node, &ed, 1);
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  std::vector<lf::BatchParams> params;
+  params.reserve(chains.size() * kGraphSteps);
+  for (size_t c = 0; c < chains.size() && e == cudaSuccess; ++c) {
+    const int dtype = chains[c].first;
+    cudaGraphNode_t prev = nullptr;
+    for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) {
+      params.push_back(chains[c].second);
+      params.back().step = s;
+      void* args[1] = {&params.back()};
+      cudaKernelNodeParams kp{};
+      kp.func = const_cast<void*>(lf::step_kernel(dtype));
+      kp.gridDim = dim3(static_cast<unsigned>(chains[c].second.tile_start[chains[c].second.n_jobs]));
+      kp.blockDim = dim3(static_cast<unsigned>(lf::kTile));
+      kp.sharedMemBytes = 0;
+      kp.kernelParams = args;
+      cudaGraphNode_t node = nullptr;
+      e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp);   // copies the parameters
+      if (e == cudaSuccess && prev) {
+        cudaGraphEdgeData ed{};
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        ed.to_port = 0;
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+        e = cudaGraphAddDependencies(g, &prev, &node, &ed, 1);
+      }
+      prev = node;
     }
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(g);
-      return cuda_fail(m, e, "building the step graph");
-    }
-    prev = node;
   }
-  cudaError_t e = cudaGraphInstantiate(&m->gexec, g, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return cuda_fail(m, e, "cudaGraphInstantiate");
+  if (e != cudaSuccess) *out = nullptr;
+  return e;
+}
+
+lf_status build_graph(lf_mesh m) {
+  const int par = static_cast<int>(m->h_st.epoch & 1u);
+  if (m->gexec[par]) return LF_OK;
+  std::vector<std::pair<int, lf::BatchParams>> chains;
+  chains.emplace_back(m->dtype, single_job_params(m, kGraphSteps));
+  cudaError_t e = make_step_graph(chains, &m->gexec[par]);
+  if (e != cudaSuccess) return cuda_fail(m, e, "building the step graph");
   return LF_OK;
 }
 
@@ -334,9 +379,8 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
   m->d_Lrp = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * (n_v + 1)));
   m->d_Lcv = static_cast<int2*>(m->dalloc(sizeof(int2) * std::max<int64_t>(nnz, 1)));
   m->d_st = static_cast<lf::DevStatus*>(m->dalloc(sizeof(lf::DevStatus)));
-  m->d_job = static_cast<lf::JobDesc*>(m->dalloc(sizeof(lf::JobDesc)));
   for (int b = 0; b < 2; ++b) m->buf[b].rows = static_cast<int2*>(m->dalloc(sizeof(int2) * n_v));
-  if (!m->d_Lrp || !m->d_Lcv || !m->d_st || !m->d_job || !m->buf[0].rows || !m->buf[1].rows) {
+  if (!m->d_Lrp || !m->d_Lcv || !m->d_st || !m->buf[0].rows || !m->buf[1].rows) {
     delete m;
     return fail(nullptr, LF_ERR_OOM, "device allocation");
   }
@@ -382,6 +426,62 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
 
 namespace lf {
 void set_last_error(const std::string& msg) { g_create_error = msg; }
+
+bool cotan_offdiag(int64_t n_v, const double* V, int64_t n_f, const int32_t* F, std::vector<int64_t>& rp,
+                   std::vector<int32_t>& col, std::vector<double>& val, std::string& why) {
+  return cotan_rows(n_v, V, n_f, F, rp, col, val, why);
+}
+
+bool mesh_ok(int64_t n_v, const double* V, int64_t n_f, const int32_t* F, std::string& why) {
+  if (!V || !F) { why = "null argument"; return false; }
+  if (n_v < 3 || n_v >= kMaxCap) { why = "n_v out of range"; return false; }
+  if (n_f < 1) { why = "n_f must be >= 1"; return false; }
+  for (int64_t f = 0; f < n_f; ++f) {
+    const int32_t a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= n_v || b >= n_v || c >= n_v) {
+      why = "face " + std::to_string(f) + " has a vertex out of range";
+      return false;
+    }
+    if (a == b || b == c || a == c) {
+      why = "face " + std::to_string(f) + " repeats a vertex";
+      return false;
+    }
+  }
+  for (int64_t i = 0; i < 3 * n_v; ++i)
+    if (!std::isfinite(V[i])) { why = "non-finite vertex coordinate"; return false; }
+  return true;
+}
+
+bool seeds_ok(int64_t n_v, const int32_t* seeds, int32_t k, std::string& why) {
+  if (!seeds || k < 1) { why = "need k >= 1 seeds"; return false; }
+  if (static_cast<int64_t>(k) + 1 > 65536) { why = "k + 1 must be <= 65536"; return false; }
+  if (k > n_v) { why = "more seeds than vertices"; return false; }
+  std::vector<char> used(static_cast<size_t>(n_v), 0);
+  for (int32_t i = 0; i < k; ++i) {
+    if (seeds[i] < 0 || seeds[i] >= n_v) { why = "seed vertex out of range"; return false; }
+    if (used[static_cast<size_t>(seeds[i])]) { why = "repeated seed vertex"; return false; }
+    used[static_cast<size_t>(seeds[i])] = 1;
+  }
+  return true;
+}
+
+bool params_valid(const lf_params& p, std::string& why) { return params_ok(p, why); }
+
+lf_status create_from_offdiag(const lf_device* dev, int64_t n_v, const std::vector<int64_t>& rp,
+                              const std::vector<int32_t>& col, const std::vector<double>& val,
+                              const lf_params& prm, lf_mesh* out) {
+  return finish_create(dev, n_v, rp, col, val, prm, out);
+}
+
+int64_t device_bytes_estimate(int64_t n_v, int64_t nnz_off, const lf_params& prm) {
+  auto r = [](int64_t b) { return (std::max<int64_t>(b, 16) + 255) & ~int64_t(255); };
+  const int64_t tiles = (n_v + kTile - 1) / kTile;
+  const int64_t cap = prm.initial_capacity > 0 ? round16(std::max<int64_t>((prm.initial_capacity + tiles - 1) / tiles, kTile))
+                                               : 3 * kTile;
+  const int64_t entries = tiles * cap;
+  return r(4 * (n_v + 1)) + r(8 * nnz_off) + r(static_cast<int64_t>(sizeof(DevStatus))) + 2 * r(8 * n_v) +
+         2 * (r(2 * entries) + r(value_bytes(prm.field_dtype) * entries)) + r(4 * n_v) /* labels */;
+}
 }  // namespace lf
 
 extern "C" {
@@ -405,23 +505,13 @@ void lf_default_params(lf_params* p) {
 
 lf_status lf_create_mesh(const lf_device* dev, const double* V, int64_t n_v, const int32_t* F, int64_t n_f,
                          const lf_params* params, lf_mesh* out) {
-  if (!out || !V || !F) return fail(nullptr, LF_ERR_INVALID, "null argument");
-  if (n_v < 3 || n_v >= kMaxCap) return fail(nullptr, LF_ERR_INVALID, "n_v out of range");
-  if (n_f < 1) return fail(nullptr, LF_ERR_INVALID, "n_f must be >= 1");
+  if (!out) return fail(nullptr, LF_ERR_INVALID, "null argument");
   lf_params prm;
   lf_default_params(&prm);
   if (params) prm = *params;
   std::string why;
   if (!params_ok(prm, why)) return fail(nullptr, LF_ERR_INVALID, why);
-  for (int64_t f = 0; f < n_f; ++f) {
-    const int32_t a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
-    if (a < 0 || b < 0 || c < 0 || a >= n_v || b >= n_v || c >= n_v)
-      return fail(nullptr, LF_ERR_INVALID, "face " + std::to_string(f) + " has a vertex out of range");
-    if (a == b || b == c || a == c)
-      return fail(nullptr, LF_ERR_INVALID, "face " + std::to_string(f) + " repeats a vertex");
-  }
-  for (int64_t i = 0; i < 3 * n_v; ++i)
-    if (!std::isfinite(V[i])) return fail(nullptr, LF_ERR_INVALID, "non-finite vertex coordinate");
+  if (!lf::mesh_ok(n_v, V, n_f, F, why)) return fail(nullptr, LF_ERR_INVALID, why);
   std::vector<int64_t> rp;
   std::vector<int32_t> col;
   std::vector<double> val;
@@ -430,7 +520,26 @@ lf_status lf_create_mesh(const lf_device* dev, const double* V, int64_t n_v, con
   } catch (const std::bad_alloc&) {
     return fail(nullptr, LF_ERR_OOM, "host allocation");
   }
-  return finish_create(dev, n_v, rp, col, val, prm, out);
+  lf_status s = finish_create(dev, n_v, rp, col, val, prm, out);
+  if (s != LF_OK) return s;
+  // the mesh itself stays on the device for the Lloyd-like update (Sec. 5)
+  lf_mesh m = *out;
+  m->d_V = static_cast<double*>(m->dalloc(sizeof(double) * 3 * static_cast<size_t>(n_v)));
+  m->d_tri = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * 3 * static_cast<size_t>(n_f)));
+  cudaError_t e = (m->d_V && m->d_tri) ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_V, V, sizeof(double) * 3 * n_v, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_tri, F, sizeof(int32_t) * 3 * n_f, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    *out = nullptr;
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? LF_ERR_OOM : LF_ERR_CUDA, "uploading the mesh");
+  }
+  m->n_f = n_f;
+  return LF_OK;
 }
 
 lf_status lf_create_mesh_csr(const lf_device* dev, int64_t n_v, const int64_t* rowptr, const int32_t* col,
@@ -468,15 +577,8 @@ lf_status lf_create_mesh_csr(const lf_device* dev, int64_t n_v, const int64_t* r
 lf_status lf_seed(lf_mesh m, const int32_t* seeds, int32_t k) {
   lf_status s = check_usable(m);
   if (s != LF_OK) return s;
-  if (!seeds || k < 1) return fail(m, LF_ERR_INVALID, "need k >= 1 seeds");
-  if (static_cast<int64_t>(k) + 1 > 65536) return fail(m, LF_ERR_INVALID, "k + 1 must be <= 65536");
-  if (k > m->n_v) return fail(m, LF_ERR_INVALID, "more seeds than vertices");
-  std::vector<char> used(static_cast<size_t>(m->n_v), 0);
-  for (int32_t i = 0; i < k; ++i) {
-    if (seeds[i] < 0 || seeds[i] >= m->n_v) return fail(m, LF_ERR_INVALID, "seed vertex out of range");
-    if (used[static_cast<size_t>(seeds[i])]) return fail(m, LF_ERR_INVALID, "repeated seed vertex");
-    used[static_cast<size_t>(seeds[i])] = 1;
-  }
+  std::string why;
+  if (!lf::seeds_ok(m->n_v, seeds, k, why)) return fail(m, LF_ERR_INVALID, why);
   auto* d_seeds = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * static_cast<size_t>(k)));
   if (!d_seeds) return fail(m, LF_ERR_OOM, "seed upload buffer");
   m->n_layers = k + 1;
@@ -487,11 +589,12 @@ lf_status lf_seed(lf_mesh m, const int32_t* seeds, int32_t k) {
   if (s == LF_OK) s = upload_status(m);
   if (s != LF_OK) return s;
   LF_CUDA(m, cudaMemcpyAsync(d_seeds, seeds, sizeof(int32_t) * k, cudaMemcpyHostToDevice, m->stream));
-  LF_CUDA(m, lf::launch_seed(m->d_job, static_cast<int>(m->n_v), k, d_seeds, m->dtype, m->stream));
+  LF_CUDA(m, lf::launch_seed(m->h_job, k, d_seeds, m->dtype, m->stream));
   LF_CUDA(m, cudaStreamSynchronize(m->stream));
   m->dfree(d_seeds);
   m->steps = 0;
   m->retries = 0;
+  m->seeds.assign(seeds, seeds + k);
   return LF_OK;
 }
 
@@ -508,12 +611,19 @@ lf_status lf_step(lf_mesh m, int32_t n_iters) {
       s = build_graph(m);
       if (s != LF_OK) return s;
       while (todo - launched >= kGraphSteps) {
-        LF_CUDA(m, cudaGraphLaunch(m->gexec, m->stream));
+        LF_CUDA(m, cudaGraphLaunch(m->gexec[m->h_st.epoch & 1u], m->stream));
         launched += kGraphSteps;
       }
     }
-    for (; launched < todo; ++launched)
-      LF_CUDA(m, lf::launch_step(m->d_job, m->num_tiles, m->dtype, m->stream));
+    if (launched < todo) {
+      // the graph launches above cover an even number of steps, so the
+      // starting parity of the remainder is still that of the current epoch
+      lf::BatchParams p = single_job_params(m, static_cast<int>(todo - launched));
+      for (int s2 = 0; launched < todo; ++launched, ++s2) {
+        p.step = s2;
+        LF_CUDA(m, lf::launch_step(p, m->dtype, m->stream));
+      }
+    }
     s = read_status(m);
     if (s != LF_OK) return s;
     m->steps = static_cast<int64_t>(m->h_st.epoch);
@@ -541,6 +651,122 @@ lf_status lf_step(lf_mesh m, int32_t n_iters) {
   return LF_OK;
 }
 
+lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters) {
+  if (!meshes || n < 1 || n > lf::kMaxJobs)
+    return fail(nullptr, LF_ERR_INVALID, "need 1 <= n <= 64 meshes");
+  if (!n_iters) return fail(nullptr, LF_ERR_INVALID, "n_iters is null");
+  for (int32_t a = 0; a < n; ++a) {
+    lf_mesh m = meshes[a];
+    lf_status s = check_usable(m);
+    if (s != LF_OK) return s;
+    if (n_iters[a] < 0) return fail(m, LF_ERR_INVALID, "n_iters must be >= 0");
+    if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed or lf_set_field must come first");
+    for (int32_t b = 0; b < a; ++b)
+      if (meshes[b] == m) return fail(m, LF_ERR_INVALID, "a mesh appears twice in the batch");
+  }
+  // the batch runs on the first mesh's stream, after every mesh's own work
+  lf_mesh m0 = meshes[0];
+  std::vector<int64_t> target(static_cast<size_t>(n));
+  for (int32_t a = 0; a < n; ++a) {
+    lf_status s = read_status(meshes[a]);
+    if (s != LF_OK) return s;
+    target[static_cast<size_t>(a)] = meshes[a]->steps + n_iters[a];
+  }
+  // one chain of launches per storage type present; the graph is rebuilt
+  // whenever the parameters of a chain change (members, buffers, parity)
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<std::pair<int, lf::BatchParams>> gkey;
+  auto drop_graph = [&]() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  };
+  lf_status result = LF_OK;
+  for (;;) {
+    // every job still running advances by the same count, so one parameter
+    // set holds for the whole chunk and finished jobs leave the launches
+    int64_t todo = kPollSteps;
+    int active = 0;
+    for (int32_t a = 0; a < n; ++a) {
+      const int64_t left = target[static_cast<size_t>(a)] - meshes[a]->steps;
+      if (left > 0) { todo = std::min(todo, left); ++active; }
+    }
+    if (active == 0) break;
+    std::vector<std::pair<int, lf::BatchParams>> chains;
+    for (int dtype = 0; dtype < 3; ++dtype) {
+      lf::BatchParams p;
+      std::memset(&p, 0, sizeof(p));
+      int tiles = 0;
+      for (int32_t a = 0; a < n; ++a) {
+        lf_mesh m = meshes[a];
+        if (m->dtype != dtype || target[static_cast<size_t>(a)] == m->steps) continue;
+        const int j = p.n_jobs++;
+        p.tile_start[j] = tiles;
+        tiles += m->num_tiles;
+        p.job[j] = m->h_job;
+        p.job[j].parity0 = static_cast<int32_t>(m->h_st.epoch & 1u);
+        p.job[j].steps = static_cast<int32_t>(todo);
+      }
+      p.tile_start[p.n_jobs] = tiles;
+      if (p.n_jobs > 0) chains.emplace_back(dtype, p);
+    }
+    int64_t launched = 0;
+    if (todo >= kGraphSteps) {
+      std::vector<std::pair<int, lf::BatchParams>> gc = chains;
+      for (auto& c : gc)
+        for (int j = 0; j < c.second.n_jobs; ++j) c.second.job[j].steps = kGraphSteps;
+      bool same = gexec && gc.size() == gkey.size();
+      for (size_t c = 0; same && c < gc.size(); ++c)
+        same = gc[c].first == gkey[c].first && std::memcmp(&gc[c].second, &gkey[c].second, sizeof(lf::BatchParams)) == 0;
+      if (!same) {
+        drop_graph();
+        cudaError_t e = make_step_graph(gc, &gexec);
+        if (e != cudaSuccess) return cuda_fail(m0, e, "building the batch graph");
+        gkey = gc;
+      }
+      while (todo - launched >= kGraphSteps) {
+        cudaError_t e = cudaGraphLaunch(gexec, m0->stream);
+        if (e != cudaSuccess) { drop_graph(); return cuda_fail(m0, e, "cudaGraphLaunch"); }
+        launched += kGraphSteps;
+      }
+    }
+    for (auto& c : chains)
+      for (int j = 0; j < c.second.n_jobs; ++j) {
+        c.second.job[j].steps = static_cast<int32_t>(todo - launched);
+        c.second.job[j].parity0 = static_cast<int32_t>((c.second.job[j].parity0 + launched) & 1);
+      }
+    for (int k = 0; launched < todo; ++launched, ++k)
+      for (auto& c : chains) {
+        c.second.step = k;
+        cudaError_t e = lf::launch_step(c.second, c.first, m0->stream);
+        if (e != cudaSuccess) { drop_graph(); return cuda_fail(m0, e, "launching a batch step"); }
+      }
+    cudaError_t e = cudaStreamSynchronize(m0->stream);
+    if (e != cudaSuccess) { drop_graph(); return cuda_fail(m0, e, "cudaStreamSynchronize"); }
+    // per job: progress, and recovery of the jobs whose step failed
+    for (int32_t a = 0; a < n; ++a) {
+      lf_mesh m = meshes[a];
+      if (target[static_cast<size_t>(a)] == m->steps) continue;
+      lf_status s = read_status(m);
+      if (s != LF_OK) { drop_graph(); return s; }
+      m->steps = static_cast<int64_t>(m->h_st.epoch);
+      if (m->h_st.err == 0u) continue;
+      if (m->h_st.err & lf::ERR_ZERO_SUM) {
+        reset_after_failure(m);
+        target[static_cast<size_t>(a)] = m->steps;          // leave it out of the rest of the batch
+        result = fail(m, LF_ERR_STATE, "a vertex summed to zero before normalisation");
+        continue;
+      }
+      const int64_t need = static_cast<int64_t>(m->h_st.need_tile);
+      s = set_tile_cap(m, std::max<int64_t>(need + need / 4, m->tile_cap + m->tile_cap / 5 + 1), true);
+      if (s == LF_OK) s = reset_after_failure(m);
+      if (s != LF_OK) { drop_graph(); return s; }
+      ++m->retries;
+    }
+  }
+  drop_graph();
+  return result;
+}
+
 lf_status lf_labels(lf_mesh m, int32_t* labels, float* maxval) {
   lf_status s = check_usable(m);
   if (s != LF_OK) return s;
@@ -556,7 +782,7 @@ lf_status lf_labels(lf_mesh m, int32_t* labels, float* maxval) {
     if (!m->d_scratch_f) { m->scratch_f_len = 0; return fail(m, LF_ERR_OOM, "value buffer"); }
     m->scratch_f_len = m->n_v;
   }
-  LF_CUDA(m, lf::launch_labels(m->d_job, static_cast<int>(m->n_v), m->dtype, m->d_labels,
+  LF_CUDA(m, lf::launch_labels(m->h_job, static_cast<int>(m->h_st.epoch & 1u), m->dtype, m->d_labels,
                                maxval ? m->d_scratch_f : nullptr, m->stream));
   LF_CUDA(m, cudaMemcpyAsync(labels, m->d_labels, sizeof(int32_t) * m->n_v, cudaMemcpyDeviceToHost, m->stream));
   if (maxval)
@@ -678,9 +904,59 @@ lf_status lf_set_field(lf_mesh m, const int64_t* rowptr, const int32_t* layer, c
   m->n_layers = n_layers;
   m->h_job.n_layers = n_layers;
   m->h_st.nnz = static_cast<unsigned long long>(nnz);
+  if (static_cast<int64_t>(m->seeds.size()) != n_layers - 1) m->seeds.clear();
   s = upload_job(m);
   if (s == LF_OK) s = upload_status(m);
   return s;
+}
+
+lf_status lf_lloyd(lf_mesh m, int32_t rounds, int32_t steps_per_round, int32_t* seeds_out) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (rounds < 0 || steps_per_round < 0) return fail(m, LF_ERR_INVALID, "rounds and steps_per_round must be >= 0");
+  if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed must come first");
+  if (!m->d_V) return fail(m, LF_ERR_STATE, "the Lloyd-like update needs a mesh made by lf_create_mesh");
+  const int64_t k = m->n_layers - 1;
+  if (static_cast<int64_t>(m->seeds.size()) != k)
+    return fail(m, LF_ERR_STATE, "the seeds of the current field are unknown (lf_seed sets them)");
+  if (m->lloyd_k != k) {
+    for (void* p : {static_cast<void*>(m->lloyd.acc), static_cast<void*>(m->lloyd.frame),
+                    static_cast<void*>(m->lloyd.best), static_cast<void*>(m->lloyd.owner),
+                    static_cast<void*>(m->lloyd.rounds), static_cast<void*>(m->d_seed_old),
+                    static_cast<void*>(m->d_seed_new)})
+      m->dfree(p);
+    m->lloyd.acc = static_cast<double*>(m->dalloc(sizeof(double) * 7 * k));
+    m->lloyd.frame = static_cast<double*>(m->dalloc(sizeof(double) * 7 * k));
+    m->lloyd.best = static_cast<unsigned long long*>(m->dalloc(sizeof(unsigned long long) * 2 * k));
+    m->lloyd.owner = static_cast<unsigned long long*>(m->dalloc(sizeof(unsigned long long) * m->n_v));
+    m->lloyd.rounds = static_cast<int32_t*>(m->dalloc(sizeof(int32_t)));
+    m->d_seed_old = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * k));
+    m->d_seed_new = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * k));
+    if (!m->lloyd.acc || !m->lloyd.frame || !m->lloyd.best || !m->lloyd.owner || !m->lloyd.rounds ||
+        !m->d_seed_old || !m->d_seed_new) {
+      m->lloyd_k = 0;
+      return fail(m, LF_ERR_OOM, "Lloyd scratch");
+    }
+    m->lloyd_k = k;
+  }
+  for (int32_t r = 0; r < rounds; ++r) {
+    s = read_status(m);
+    if (s != LF_OK) return s;
+    const int cur = static_cast<int>(m->h_st.epoch & 1u);
+    std::vector<int32_t> fresh(static_cast<size_t>(k));
+    LF_CUDA(m, cudaMemcpyAsync(m->d_seed_old, m->seeds.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice,
+                               m->stream));
+    LF_CUDA(m, lf::launch_lloyd(m->h_job, cur, m->d_V, m->d_tri, static_cast<int>(m->n_f), static_cast<int>(k),
+                                m->d_seed_old, m->d_seed_new, m->lloyd, m->stream));
+    LF_CUDA(m, cudaMemcpyAsync(fresh.data(), m->d_seed_new, sizeof(int32_t) * k, cudaMemcpyDeviceToHost,
+                               m->stream));
+    LF_CUDA(m, cudaStreamSynchronize(m->stream));
+    s = lf_seed(m, fresh.data(), static_cast<int32_t>(k));     // the new partition starts from the new seeds
+    if (s == LF_OK) s = lf_step(m, steps_per_round);
+    if (s != LF_OK) return s;
+  }
+  if (seeds_out) std::memcpy(seeds_out, m->seeds.data(), sizeof(int32_t) * k);
+  return LF_OK;
 }
 
 lf_status lf_stats(lf_mesh m, lf_stats_t* out) {

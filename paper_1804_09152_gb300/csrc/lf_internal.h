@@ -6,6 +6,9 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
+
+#include "../../include/lf.h"
 
 namespace lf {
 
@@ -47,32 +50,48 @@ struct Coefs {
   float dt, mu, w_cc, w_cb, a_cc, a_cb, e_cc, e_cb, e_bc;
 };
 
-// Device-resident job descriptor.  Kernels read it every launch, so the host
-// can grow buffers without re-capturing a CUDA graph.
+// One job of a step launch: pointers, sizes and coefficients.  Passed to the
+// kernel by value (inside BatchParams), so a launch reads no descriptor from
+// memory; the host rebuilds the parameters when anything in it changes.
 struct JobDesc {
   int32_t n_v;
   int32_t n_layers;          // k + 1; the base layer is n_layers - 1
-  int32_t num_tiles;         // CTAs of one step launch
+  int32_t num_tiles;         // CTAs of this job in one step launch
   int32_t tile_cap;          // entries per tile segment (multiple of 16)
+  int32_t parity0;           // the input of launch `step` is buf[(parity0 + step) & 1]
+  int32_t steps;             // launches with step >= steps leave this job alone
   const int32_t* L_rowptr;   // n_v + 1, off-diagonal entries only
   const int2* L_colval;      // (column, float bits of L_ij), j != i
   FieldBuf buf[2];
   DevStatus* st;
   Coefs c;
-  int32_t pad[3];
+  int32_t pad;
+};
+
+// Parameters of one step launch: up to kMaxJobs jobs whose tiles are laid
+// out one after another in the grid (job j owns CTAs tile_start[j] ..
+// tile_start[j + 1] - 1).
+constexpr int kMaxJobs = 64;
+struct BatchParams {
+  int32_t n_jobs;
+  int32_t step;
+  int32_t tile_start[kMaxJobs + 1];
+  int32_t pad;
+  JobDesc job[kMaxJobs];
 };
 
 constexpr int kTile = 256;   // vertices per tile = threads per step CTA
 
 // Register slots of the step kernel's fast path.
 int step_slots();
-// Kernel entry of the step for a storage type (0 f32, 1 bf16, 2 f16).
+// Kernel entry of the step for a storage type (0 f32, 1 bf16, 2 f16); its
+// only argument is a BatchParams.
 const void* step_kernel(int dtype);
-// One step launch with programmatic stream serialisation.
-cudaError_t launch_step(const JobDesc* d_job, int num_tiles, int dtype, cudaStream_t s);
-cudaError_t launch_seed(const JobDesc* d_job, int n_v, int k, const int32_t* d_seeds, int dtype,
-                        cudaStream_t s);
-cudaError_t launch_labels(const JobDesc* d_job, int n_v, int dtype, int32_t* d_labels, float* d_maxval,
+// One step launch over the jobs in p, with programmatic stream serialisation.
+cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s);
+// The seed and label kernels take one job by value.
+cudaError_t launch_seed(const JobDesc& job, int k, const int32_t* d_seeds, int dtype, cudaStream_t s);
+cudaError_t launch_labels(const JobDesc& job, int buf, int dtype, int32_t* d_labels, float* d_maxval,
                           cudaStream_t s);
 // Copies the rows of `from` into the segments of `to` (tile_cap may differ).
 cudaError_t launch_relayout(const int2* rows_from, const uint16_t* ids_from, const void* vals_from,
@@ -84,7 +103,38 @@ cudaError_t launch_narrow(const float* src, void* dst, int64_t n, int dtype, cud
 
 inline int value_bytes(int dtype) { return dtype == 0 ? 4 : 2; }
 
+// Device scratch of one Lloyd-like seed update (k cells, n_v vertices).
+struct LloydScratch {
+  double* acc;                  // k * 7: area, area * barycentre, area * normal
+  double* frame;                // k * 7: centre of mass, unit direction, valid
+  unsigned long long* best;     // k * 2: nearest |s| (bits), its lowest face id
+  unsigned long long* owner;    // n_v: conflict resolution
+  int32_t* rounds;              // 1: rounds the resolution took
+};
+// New seeds (Sec. 5) from the field in job.buf[buf]: V (n_v x 3 FP64) and tri
+// (n_f x 3) are the mesh; old_seed and new_seed hold k vertex ids on the device.
+cudaError_t launch_lloyd(const JobDesc& job, int buf, const double* V, const int32_t* tri, int n_f, int k,
+                         const int32_t* old_seed, int32_t* new_seed, LloydScratch sc, cudaStream_t s);
+
 // Message returned by lf_last_error(NULL) (thread-local).
 void set_last_error(const std::string& msg);
+
+// Host helpers shared with the serving runtime (lf_server.cpp).
+// Cotangent operator of a triangle mesh as off-diagonal FP64 CSR; false (with
+// a reason) on a zero-area face.
+bool cotan_offdiag(int64_t n_v, const double* V, int64_t n_f, const int32_t* F, std::vector<int64_t>& rp,
+                   std::vector<int32_t>& col, std::vector<double>& val, std::string& why);
+// Checks faces (in range, no repeated vertex) and coordinates (finite).
+bool mesh_ok(int64_t n_v, const double* V, int64_t n_f, const int32_t* F, std::string& why);
+// Checks seeds: 1 <= k <= 65535, in range, no vertex twice.
+bool seeds_ok(int64_t n_v, const int32_t* seeds, int32_t k, std::string& why);
+// Validates parameters as lf_create_mesh does.
+bool params_valid(const lf_params& p, std::string& why);
+// lf_create_mesh from a prepared off-diagonal operator.
+lf_status create_from_offdiag(const lf_device* dev, int64_t n_v, const std::vector<int64_t>& rp,
+                              const std::vector<int32_t>& col, const std::vector<double>& val,
+                              const lf_params& prm, lf_mesh* out);
+// Device bytes lf_create_mesh would allocate for this operator and parameters.
+int64_t device_bytes_estimate(int64_t n_v, int64_t nnz_off, const lf_params& prm);
 
 }  // namespace lf

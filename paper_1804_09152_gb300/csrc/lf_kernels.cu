@@ -71,9 +71,13 @@ __device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcont
 __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 constexpr int kBlock = kTile;   // threads (= vertices) per CTA
-constexpr int kSlots = 6;       // register map slots of the fast path
-constexpr int kOwn = 4;         // own-row entries the fast path accepts
+#ifndef LF_SLOTS
+#define LF_SLOTS 6
+#endif
+constexpr int kSlots = LF_SLOTS; // register map slots of the fast path
 constexpr int kChunk = 4;       // neighbours fetched per batch
+constexpr int kPool = 4;        // medium-path maps per CTA
+constexpr int kMed = 32;        // slots of a medium-path map
 
 // Per-vertex quantities of the closed-form update (class coefficients).
 struct VertexSums {
@@ -91,8 +95,12 @@ struct Update {
     const int n = s.nC + s.hasb;
     fn = static_cast<float>(n);
     fnc = static_cast<float>(s.nC);
-    sumA = c.a_cc * (fnc - 1.0f) * s.sG + (s.hasb ? c.a_cb * (fnc * s.Gb + s.sG) : 0.0f);
-    sumW = c.w_cc * (fnc - 1.0f) * s.sF + (s.hasb ? c.w_cb * (fnc * s.Fb + s.sF) : 0.0f);
+    // explicit roundings throughout (no contraction left to the compiler), so
+    // that every code path that inlines this gives bit-identical results
+    const float bA = s.hasb ? __fmul_rn(c.a_cb, __fmaf_rn(fnc, s.Gb, s.sG)) : 0.0f;
+    const float bW = s.hasb ? __fmul_rn(c.w_cb, __fmaf_rn(fnc, s.Fb, s.sF)) : 0.0f;
+    sumA = __fmaf_rn(__fmul_rn(c.a_cc, __fsub_rn(fnc, 1.0f)), s.sG, bA);
+    sumW = __fmaf_rn(__fmul_rn(c.w_cc, __fsub_rn(fnc, 1.0f)), s.sF, bW);
     mun = c.mu / fn;
     sqFb = s.sqFb;
   }
@@ -101,16 +109,17 @@ struct Update {
                                          const Coefs& c) const {
     float A, W, R;
     if (is_base) {
-      A = c.a_cb * s.sG;
-      W = c.w_cb * s.sF;
-      R = c.e_bc * s.r;
+      A = __fmul_rn(c.a_cb, s.sG);
+      W = __fmul_rn(c.w_cb, s.sF);
+      R = __fmul_rn(c.e_bc, s.r);
     } else {
-      A = c.a_cc * (s.sG - g) + (s.hasb ? c.a_cb * s.Gb : 0.0f);
-      W = c.w_cc * (s.sF - f) + (s.hasb ? c.w_cb * s.Fb : 0.0f);
-      R = c.e_cc * (s.r - sqf) + (s.hasb ? c.e_cb * sqFb : 0.0f);
+      A = __fmaf_rn(c.a_cc, __fsub_rn(s.sG, g), s.hasb ? __fmul_rn(c.a_cb, s.Gb) : 0.0f);
+      W = __fmaf_rn(c.w_cc, __fsub_rn(s.sF, f), s.hasb ? __fmul_rn(c.w_cb, s.Fb) : 0.0f);
+      R = __fmaf_rn(c.e_cc, __fsub_rn(s.r, sqf), s.hasb ? __fmul_rn(c.e_cb, sqFb) : 0.0f);
     }
-    const float d = -mun * (0.5f * (fn * A - sumA) + (fn * W - sumW)) + mun * sqf * R;
-    float v = f + d * c.dt;
+    const float inner = __fmaf_rn(0.5f, __fmaf_rn(fn, A, -sumA), __fmaf_rn(fn, W, -sumW));
+    const float d = __fmaf_rn(-mun, inner, __fmul_rn(__fmul_rn(mun, sqf), R));
+    float v = __fmaf_rn(d, c.dt, f);
     if (v > 1.0f) v = 1.0f;
     if (v <= 0.0f) v = 0.0f;
     return v;
@@ -179,7 +188,7 @@ struct Neighbourhood {
       const int2 rj = __ldg(rows + cv.x);
       for (int p = rj.x; p < rj.x + rj.y; ++p) {
         const int l = __ldg(Fid + p);
-        if (l == lay) { G += lij * V::load(Fval + p); break; }
+        if (l == lay) { G = __fadd_rn(G, __fmul_rn(lij, V::load(Fval + p))); break; }
         if (l > lay) break;
       }
     }
@@ -187,29 +196,24 @@ struct Neighbourhood {
   }
 };
 
-// Register map of the fast path: layer id (-1 = empty) and G per slot; F is
-// kept for the first kOwn slots, which hold the vertex's own row (the other
-// slots are layers absent from it, F = 0).
+// Register map of the fast path: layer id (-1 = empty), G and F per slot.
 struct SlotMap {
   int id[kSlots];
   float g[kSlots];
-  float f[kOwn];
+  float f[kSlots];
   int cnt;
 
   __device__ __forceinline__ void clear() {
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) { id[s] = -1; g[s] = 0.0f; }
-#pragma unroll
-    for (int s = 0; s < kOwn; ++s) f[s] = 0.0f;
+    for (int s = 0; s < kSlots; ++s) { id[s] = -1; g[s] = 0.0f; f[s] = 0.0f; }
     cnt = 0;
   }
-  __device__ __forceinline__ float fv(int s) const { return s < kOwn ? f[s < kOwn ? s : 0] : 0.0f; }
   // Adds x to the slot of layer l, opening a slot if needed.  False when full.
   __device__ __forceinline__ bool add(int l, float x) {
     bool found = false;
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
-      if (s < cnt && !found && id[s] == l) { g[s] += x; found = true; }
+      if (s < cnt && !found && id[s] == l) { g[s] = __fadd_rn(g[s], x); found = true; }
     }
     if (found) return true;
     if (cnt >= kSlots) return false;
@@ -217,6 +221,45 @@ struct SlotMap {
     for (int s = 0; s < kSlots; ++s) {
       if (s == cnt) { id[s] = l; g[s] = x; }
     }
+    ++cnt;
+    return true;
+  }
+  __device__ __forceinline__ void cswap(int a, int b) {
+    const bool sw = static_cast<unsigned>(id[a]) > static_cast<unsigned>(id[b]);   // -1 sorts last
+    const int ia = id[a], ib = id[b];
+    const float ga = g[a], gb = g[b], fa = f[a], fb = f[b];
+    id[a] = sw ? ib : ia; id[b] = sw ? ia : ib;
+    g[a] = sw ? gb : ga;  g[b] = sw ? ga : gb;
+    f[a] = sw ? fb : fa;  f[b] = sw ? fa : fb;
+  }
+  // Sorting network on the slots (ids are distinct): the optimal five
+  // exchanges for four slots, odd-even transposition otherwise.
+  __device__ __forceinline__ void sort() {
+    if constexpr (kSlots == 4) {
+      cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
+    } else {
+#pragma unroll
+      for (int r = 0; r < kSlots; ++r)
+#pragma unroll
+        for (int a = r & 1; a + 1 < kSlots; a += 2) cswap(a, a + 1);
+    }
+  }
+};
+
+// Medium path: a map of kMed slots in shared memory, one of kPool per CTA,
+// taken by the (rare) threads whose union outgrows the register map.
+struct MedMap {
+  int* id;
+  float* g;
+  float* f;
+  int cnt;
+  __device__ bool add(int l, float x, float fv) {
+    for (int s = 0; s < cnt; ++s)
+      if (id[s] == l) { g[s] = __fadd_rn(g[s], x); return true; }
+    if (cnt == kMed) return false;
+    id[cnt] = l;
+    g[cnt] = x;
+    f[cnt] = fv;
     ++cnt;
     return true;
   }
@@ -239,69 +282,94 @@ __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* s_red) {
 // ---------------------------------------------------------------------------
 // the step kernel
 // ---------------------------------------------------------------------------
+enum : int { kFast = 0, kMedium = 1, kSlow = 2 };
+
 template <int DT>
-__global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __restrict__ job) {
+__global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_constant__ BatchParams P) {
   using V = Val<DT>;
   using T = typename V::T;
   constexpr int kWarps = kBlock / 32;
-  __shared__ uint32_t s_epoch, s_abort;
+  __shared__ uint32_t s_err;
+  __shared__ int s_pool;
   __shared__ unsigned s_red[kWarps];
   __shared__ int s_warp_cnt[kWarps];
+  __shared__ int s_med_id[kPool][kMed];
+  __shared__ float s_med_g[kPool][kMed];
+  __shared__ float s_med_f[kPool][kMed];
 
   wait_previous_grid();
   allow_next_grid();
 
+  // ---- the job of this CTA (uniform): last j with tile_start[j] <= blockIdx.x
+  int lo = 0, hi = P.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.tile_start[mid] <= static_cast<int>(blockIdx.x)) lo = mid; else hi = mid - 1;
+  }
+  const JobDesc& J = P.job[lo];
+  if (P.step >= J.steps) return;
+
   const int t = threadIdx.x;
   const int lane = t & 31;
   const int warp = t >> 5;
-  DevStatus* st = job->st;
-  if (t == 0) {
-    s_abort = ld_relaxed_u32(&st->err);
-    s_epoch = ld_relaxed_u32(&st->epoch);
-  }
-  __syncthreads();
-  if (s_abort) return;
-
-  const int tile = blockIdx.x;
-  const uint32_t epoch = s_epoch;
-  const int n_v = job->n_v;
-  const int base = job->n_layers - 1;
-  const int cap = job->tile_cap;
-  const FieldBuf in = job->buf[epoch & 1u];
-  const FieldBuf out = job->buf[(epoch & 1u) ^ 1u];
-  const Coefs c = job->c;
+  const int tile = static_cast<int>(blockIdx.x) - P.tile_start[lo];
+  const int n_v = J.n_v;
+  const int base = J.n_layers - 1;
+  const int cap = J.tile_cap;
+  const int par = (J.parity0 + P.step) & 1;
+  const FieldBuf in = J.buf[par];
+  const FieldBuf out = J.buf[par ^ 1];
+  const Coefs& c = J.c;
+  DevStatus* st = J.st;
 
   Neighbourhood<DT> nb;
   nb.rows = in.rows;
   nb.Fid = in.ids;
   nb.Fval = static_cast<const T*>(in.vals);
-  nb.Lcv = job->L_colval;
+  nb.Lcv = J.L_colval;
   nb.dsum = 0.0f;
+  nb.p0 = nb.p1 = nb.q0 = nb.q1 = 0;
 
+  // the first loads do not depend on the error word: issue them before the
+  // barrier that publishes it
   const int i = tile * kBlock + t;
+  if (i < n_v) {
+    const int2 ri = __ldg(nb.rows + i);
+    nb.p0 = ri.x;
+    nb.p1 = ri.x + ri.y;
+    nb.q0 = __ldg(J.L_rowptr + i);
+    nb.q1 = __ldg(J.L_rowptr + i + 1);
+  }
+  if (t == 0) {
+    s_err = ld_relaxed_u32(&st->err);
+    s_pool = 0;
+  }
+  __syncthreads();
+  if (s_err) return;                 // an earlier step of this job failed
+
   SlotMap mp;
   mp.clear();
-  bool slow = false, zero_sum = false;
-  int kept = 0, nsk = 0, own = 0;
+  int mode = kFast;
+  bool zero_sum = false;
+  int kept = 0, nsk = 0;
+  const int own = nb.p1 - nb.p0;
   float vnew[kSlots];
   bool keep[kSlots];
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) { vnew[s] = 0.0f; keep[s] = false; }
   VertexSums S = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, 0};
   float tot = 0.0f;
+  MedMap med;
+  med.cnt = 0;
+  med.id = nullptr;
+  med.g = med.f = nullptr;
 
   if (i < n_v) {
-    const int2 ri = __ldg(nb.rows + i);
-    nb.p0 = ri.x;
-    nb.p1 = ri.x + ri.y;
-    own = ri.y;
-    nb.q0 = __ldg(job->L_rowptr + i);
-    nb.q1 = __ldg(job->L_rowptr + i + 1);
-    if (own > kOwn) {
-      slow = true;
+    if (own > kSlots) {
+      mode = kMedium;
     } else {
 #pragma unroll
-      for (int s = 0; s < kOwn; ++s) {
+      for (int s = 0; s < kSlots; ++s) {
         if (s < own) {
           mp.id[s] = __ldg(nb.Fid + nb.p0 + s);
           mp.f[s] = V::load(nb.Fval + nb.p0 + s);
@@ -334,7 +402,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __r
           nb.dsum += lij[k];
         }
       }
-      if (slow) continue;
+      if (mode != kFast) continue;
       // the first two entries of each row of the batch; -2 marks "no entry"
       constexpr int kE = 2 * kChunk;
       int eid[kE];
@@ -345,11 +413,11 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __r
         ex[2 * k] = ex[2 * k + 1] = 0.0f;
         if (rn[k] > 0) {
           eid[2 * k] = __ldg(nb.Fid + r0[k]);
-          ex[2 * k] = lij[k] * V::load(nb.Fval + r0[k]);
+          ex[2 * k] = __fmul_rn(lij[k], V::load(nb.Fval + r0[k]));
         }
         if (rn[k] > 1) {
           eid[2 * k + 1] = __ldg(nb.Fid + r0[k] + 1);
-          ex[2 * k + 1] = lij[k] * V::load(nb.Fval + r0[k] + 1);
+          ex[2 * k + 1] = __fmul_rn(lij[k], V::load(nb.Fval + r0[k] + 1));
         }
       }
       // entries whose layer already has a slot: slot x entry compare matrix,
@@ -362,7 +430,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __r
 #pragma unroll
         for (int e = 0; e < kE; ++e) {
           const bool m = eid[e] == mp.id[s];
-          mp.g[s] = m ? mp.g[s] + ex[e] : mp.g[s];
+          mp.g[s] = m ? __fadd_rn(mp.g[s], ex[e]) : mp.g[s];
           hit[e] = hit[e] || m;
         }
       }
@@ -373,48 +441,109 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __r
       if (!all_hit) {
 #pragma unroll
         for (int e = 0; e < kE; ++e)
-          if (!hit[e] && !mp.add(eid[e], ex[e])) slow = true;
+          if (!hit[e] && mode == kFast && !mp.add(eid[e], ex[e])) mode = kMedium;
       }
       // rows with more than two entries
 #pragma unroll
       for (int k = 0; k < kChunk; ++k)
-        for (int p = r0[k] + 2; p < r0[k] + rn[k] && !slow; ++p)
-          if (!mp.add(__ldg(nb.Fid + p), lij[k] * V::load(nb.Fval + p))) slow = true;
+        for (int p = r0[k] + 2; p < r0[k] + rn[k] && mode == kFast; ++p)
+          if (!mp.add(__ldg(nb.Fid + p), __fmul_rn(lij[k], V::load(nb.Fval + p)))) mode = kMedium;
     }
+  }
 
-    if (!slow) {
+  // ---- medium path: a shared-memory map for unions beyond the register map
+  if (mode == kMedium) {
+    const int slot = atomicAdd(&s_pool, 1);
+    mode = kSlow;
+    if (slot < kPool && own <= kMed) {
+      med.id = s_med_id[slot];
+      med.g = s_med_g[slot];
+      med.f = s_med_f[slot];
+      bool ok = true;
+      for (int p = nb.p0; p < nb.p1; ++p) ok = ok && med.add(__ldg(nb.Fid + p), 0.0f, V::load(nb.Fval + p));
+      for (int q = nb.q0; q < nb.q1 && ok; ++q) {
+        const int2 cv = __ldg(nb.Lcv + q);
+        const float lij = __int_as_float(cv.y);
+        const int2 rj = __ldg(nb.rows + cv.x);
+        for (int p = rj.x; p < rj.x + rj.y && ok; ++p)
+          ok = med.add(__ldg(nb.Fid + p), __fmul_rn(lij, V::load(nb.Fval + p)), 0.0f);
+      }
+      if (ok) {
+        mode = kMedium;
+        for (int s = 0; s < own; ++s) med.g[s] = fmaf(-nb.dsum, med.f[s], med.g[s]);
+        // ascending layer order (insertion sort), so that every per-vertex sum
+        // below runs in the same order as on the other paths
+        for (int s = 1; s < med.cnt; ++s) {
+          const int li = med.id[s];
+          const float gi = med.g[s], fi = med.f[s];
+          int u = s - 1;
+          for (; u >= 0 && med.id[u] > li; --u) {
+            med.id[u + 1] = med.id[u];
+            med.g[u + 1] = med.g[u];
+            med.f[u + 1] = med.f[u];
+          }
+          med.id[u + 1] = li;
+          med.g[u + 1] = gi;
+          med.f[u + 1] = fi;
+        }
+      }
+    }
+  }
+
+  if (i < n_v) {
+    if (mode == kFast) {
       // ---- fast path: diagonal, skeleton, update over the register map ------
 #pragma unroll
-      for (int s = 0; s < kOwn; ++s)
+      for (int s = 0; s < kSlots; ++s)
         if (s < own) mp.g[s] = fmaf(-nb.dsum, mp.f[s], mp.g[s]);
-      float sq[kOwn];
+      // slots in ascending layer order (empty slots, id -1, last): the sums
+      // below then run in the same order as on the other paths, and the row
+      // is written in slot order
+      mp.sort();
+      float sq[kSlots];
 #pragma unroll
-      for (int s = 0; s < kOwn; ++s) sq[s] = (s < own) ? sqrtf(mp.f[s]) : 0.0f;
+      for (int s = 0; s < kSlots; ++s) sq[s] = sqrtf(mp.f[s]);
       bool ins[kSlots];
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) ins[s] = false;
-#pragma unroll
       for (int s = 0; s < kSlots; ++s) {
-        if (s < mp.cnt) {
-          ins[s] = in_skeleton(mp.fv(s), mp.g[s]);
-          if (ins[s]) add_to_sums(S, mp.id[s] == base, mp.fv(s), mp.g[s], s < kOwn ? sq[s < kOwn ? s : 0] : 0.0f);
-        }
+        ins[s] = s < mp.cnt && in_skeleton(mp.f[s], mp.g[s]);
+        if (ins[s]) add_to_sums(S, mp.id[s] == base, mp.f[s], mp.g[s], sq[s]);
       }
       const Update U(S, c);
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
-        if (s < mp.cnt && ins[s]) {
-          vnew[s] = U.value(mp.id[s] == base, mp.fv(s), mp.g[s], s < kOwn ? sq[s < kOwn ? s : 0] : 0.0f, S, c);
+        if (ins[s]) {
+          vnew[s] = U.value(mp.id[s] == base, mp.f[s], mp.g[s], sq[s], S, c);
           tot += vnew[s];
         }
       }
       if (!(tot > 0.0f)) zero_sum = true;
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
-        if (s < mp.cnt && ins[s]) {
+        if (ins[s]) {
           const float vs = V::widen(V::round(vnew[s] / tot));
           if (vs != 0.0f) { keep[s] = true; vnew[s] = vs; ++kept; }
         }
+      }
+    } else if (mode == kMedium) {
+      // ---- medium path: the same update over the shared-memory map ----------
+      for (int s = 0; s < med.cnt; ++s)
+        if (in_skeleton(med.f[s], med.g[s])) add_to_sums(S, med.id[s] == base, med.f[s], med.g[s], sqrtf(med.f[s]));
+      const Update U(S, c);
+      for (int s = 0; s < med.cnt; ++s) {
+        if (in_skeleton(med.f[s], med.g[s])) {
+          med.g[s] = U.value(med.id[s] == base, med.f[s], med.g[s], sqrtf(med.f[s]), S, c);
+          tot += med.g[s];
+        } else {
+          med.f[s] = -1.0f;                      // not in the skeleton
+        }
+      }
+      if (!(tot > 0.0f)) zero_sum = true;
+      for (int s = 0; s < med.cnt; ++s) {
+        if (med.f[s] < 0.0f) continue;
+        const float vs = V::widen(V::round(med.g[s] / tot));
+        if (vs != 0.0f) { med.g[s] = vs; ++kept; }
+        else med.f[s] = -1.0f;
       }
     } else {
       // ---- slow path: the union in increasing id order, three passes -------
@@ -456,7 +585,6 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __r
   }
   const int local_excl = warp_off + x - kept;
   const unsigned tile_sk = block_sum(static_cast<unsigned>(nsk), s_red);
-  const unsigned tile_io = block_sum(static_cast<unsigned>(own + kept), s_red);
 
   bool write = !bad_sum;
   if (t == 0 && bad_sum) atomicOr(&st->err, ERR_ZERO_SUM);
@@ -473,16 +601,22 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __r
     const int off = tile * cap + local_excl;
     out.rows[i] = make_int2(off, kept);
     T* ov = static_cast<T*>(out.vals);
-    if (!slow) {
+    if (mode == kFast) {
+      int o = off;
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
-        if (s >= mp.cnt || !keep[s]) continue;
-        int rank = 0;
-#pragma unroll
-        for (int u = 0; u < kSlots; ++u)
-          if (u < mp.cnt) rank += (keep[u] && mp.id[u] < mp.id[s]) ? 1 : 0;
-        out.ids[off + rank] = static_cast<uint16_t>(mp.id[s]);
-        ov[off + rank] = V::round(vnew[s]);
+        if (!keep[s]) continue;
+        out.ids[o] = static_cast<uint16_t>(mp.id[s]);
+        ov[o] = V::round(vnew[s]);
+        ++o;
+      }
+    } else if (mode == kMedium) {
+      int o = off;
+      for (int s = 0; s < med.cnt; ++s) {
+        if (med.f[s] < 0.0f) continue;
+        out.ids[o] = static_cast<uint16_t>(med.id[s]);
+        ov[o] = V::round(med.g[s]);
+        ++o;
       }
     } else {
       const Update U(S, c);
@@ -501,23 +635,23 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __r
     }
   }
 
-  // ---- end of step: the last CTA commits the step ---------------------------
+  // ---- end of step: the last CTA of the job commits the step ----------------
   if (t == 0) {
     atomicAdd(&st->skeleton_step, static_cast<unsigned long long>(tile_sk));
-    atomicAdd(&st->nnz_io_step, static_cast<unsigned long long>(tile_io));
     atomicAdd(&st->nnz_step, static_cast<unsigned long long>(tile_total));
     __threadfence();
     const uint32_t prev = atomicAdd(&st->done, 1u);
-    if (prev == gridDim.x - 1u) {
+    if (prev == static_cast<uint32_t>(J.num_tiles) - 1u) {
       __threadfence();
       if (ld_relaxed_u32(&st->err) == 0u) {
+        const unsigned long long nin = ld_relaxed(&st->nnz);
+        const unsigned long long nout = ld_relaxed(&st->nnz_step);
         st->skeleton_total = ld_relaxed(&st->skeleton_total) + ld_relaxed(&st->skeleton_step);
-        st->nnz_io_total = ld_relaxed(&st->nnz_io_total) + ld_relaxed(&st->nnz_io_step);
-        st->nnz = ld_relaxed(&st->nnz_step);
-        st->epoch = epoch + 1u;
+        st->nnz_io_total = ld_relaxed(&st->nnz_io_total) + nin + nout;
+        st->nnz = nout;
+        st->epoch = st->epoch + 1u;
       }
       st->skeleton_step = 0ull;
-      st->nnz_io_step = 0ull;
       st->nnz_step = 0ull;
       st->done = 0u;
       __threadfence();
@@ -529,35 +663,34 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const JobDesc* __r
 // seeding, labels, relayout, conversions
 // ---------------------------------------------------------------------------
 template <int DT>
-__global__ void seed_fill_kernel(const JobDesc* __restrict__ job, int n_v, int base) {
+__global__ void seed_fill_kernel(const __grid_constant__ JobDesc job, int base) {
   using V = Val<DT>;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_v) return;
-  const FieldBuf b = job->buf[0];
+  if (i >= job.n_v) return;
+  const FieldBuf b = job.buf[0];
   const int tile = i / kTile;
-  const int off = tile * job->tile_cap + (i - tile * kTile);
+  const int off = tile * job.tile_cap + (i - tile * kTile);
   b.rows[i] = make_int2(off, 1);
   b.ids[off] = static_cast<uint16_t>(base);
   static_cast<typename V::T*>(b.vals)[off] = V::round(1.0f);
 }
 
-__global__ void seed_scatter_kernel(const JobDesc* __restrict__ job, int k, const int32_t* __restrict__ seeds) {
+__global__ void seed_scatter_kernel(const __grid_constant__ JobDesc job, int k, const int32_t* __restrict__ seeds) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= k) return;
   const int v = seeds[s];
   const int tile = v / kTile;
-  job->buf[0].ids[tile * job->tile_cap + (v - tile * kTile)] = static_cast<uint16_t>(s);
+  job.buf[0].ids[tile * job.tile_cap + (v - tile * kTile)] = static_cast<uint16_t>(s);
 }
 
 template <int DT>
-__global__ void labels_kernel(const JobDesc* __restrict__ job, int n_v, int32_t* __restrict__ labels,
+__global__ void labels_kernel(const __grid_constant__ JobDesc job, int buf, int32_t* __restrict__ labels,
                               float* __restrict__ maxval) {
   using V = Val<DT>;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_v) return;
-  const uint32_t epoch = job->st->epoch;
-  const FieldBuf b = job->buf[epoch & 1u];
-  const int base = job->n_layers - 1;
+  if (i >= job.n_v) return;
+  const FieldBuf b = job.buf[buf];
+  const int base = job.n_layers - 1;
   const int2 r = b.rows[i];
   int best = -1;
   float bv = -1.0f;
@@ -601,7 +734,7 @@ __global__ void narrow_kernel(const float* __restrict__ src, void* __restrict__ 
   if (i < n) static_cast<typename V::T*>(dst)[i] = V::round(src[i]);
 }
 
-using StepFn = void (*)(const JobDesc*);
+using StepFn = void (*)(const BatchParams);
 const StepFn kStepFns[3] = {&step_kernel_impl<0>, &step_kernel_impl<1>, &step_kernel_impl<2>};
 
 }  // namespace
@@ -610,9 +743,9 @@ int step_slots() { return kSlots; }
 
 const void* step_kernel(int dtype) { return reinterpret_cast<const void*>(kStepFns[dtype]); }
 
-cudaError_t launch_step(const JobDesc* d_job, int num_tiles, int dtype, cudaStream_t s) {
+cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(num_tiles));
+  cfg.gridDim = dim3(static_cast<unsigned>(p.tile_start[p.n_jobs]));
   cfg.blockDim = dim3(kBlock);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
@@ -621,7 +754,7 @@ cudaError_t launch_step(const JobDesc* d_job, int num_tiles, int dtype, cudaStre
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kStepFns[dtype], d_job);
+  return cudaLaunchKernelEx(&cfg, kStepFns[dtype], p);
 }
 
 #define LF_DISPATCH(dtype, KERNEL, GRID, BLOCK, STREAM, ...)                       \
@@ -631,18 +764,17 @@ cudaError_t launch_step(const JobDesc* d_job, int num_tiles, int dtype, cudaStre
     default: KERNEL<2><<<(GRID), (BLOCK), 0, (STREAM)>>>(__VA_ARGS__); break;       \
   }
 
-cudaError_t launch_seed(const JobDesc* d_job, int n_v, int k, const int32_t* d_seeds, int dtype,
-                        cudaStream_t s) {
-  const int blocks = (n_v + 255) / 256;
-  LF_DISPATCH(dtype, seed_fill_kernel, blocks, 256, s, d_job, n_v, k);
-  seed_scatter_kernel<<<(k + 255) / 256, 256, 0, s>>>(d_job, k, d_seeds);
+cudaError_t launch_seed(const JobDesc& job, int k, const int32_t* d_seeds, int dtype, cudaStream_t s) {
+  const int blocks = (job.n_v + 255) / 256;
+  LF_DISPATCH(dtype, seed_fill_kernel, blocks, 256, s, job, k);
+  seed_scatter_kernel<<<(k + 255) / 256, 256, 0, s>>>(job, k, d_seeds);
   return cudaGetLastError();
 }
 
-cudaError_t launch_labels(const JobDesc* d_job, int n_v, int dtype, int32_t* d_labels, float* d_maxval,
+cudaError_t launch_labels(const JobDesc& job, int buf, int dtype, int32_t* d_labels, float* d_maxval,
                           cudaStream_t s) {
-  const int blocks = (n_v + 255) / 256;
-  LF_DISPATCH(dtype, labels_kernel, blocks, 256, s, d_job, n_v, d_labels, d_maxval);
+  const int blocks = (job.n_v + 255) / 256;
+  LF_DISPATCH(dtype, labels_kernel, blocks, 256, s, job, buf, d_labels, d_maxval);
   return cudaGetLastError();
 }
 

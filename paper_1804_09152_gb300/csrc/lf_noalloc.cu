@@ -1,14 +1,14 @@
 // lf_step_noalloc: one time-iteration for callers that cannot allocate.
 //
-// The regular entry points allocate the job descriptor and the step's status
+// The regular entry points allocate the field buffers and the step's status
 // words with cudaMalloc (or the lf_device hooks).  Some callers own every byte
 // of device memory themselves -- a framework with its own pool, a service that
 // allocates only at start-up, code running where allocation is not allowed --
 // and pass in all inputs and outputs.  For them the step kernel's scratch (the
-// job descriptor it reads and the status and counter words it updates) lives
-// in the file-scope array below, which every GPU that loads this library holds
-// until the process exits.  Nothing here calls cudaMalloc, cudaFree or any
-// allocating routine.
+// status and counter words it updates) lives in the file-scope array below,
+// which every GPU that loads this library holds until the process exits.
+// Nothing here calls cudaMalloc, cudaFree or any allocating routine.  The job
+// descriptor itself travels in the launch parameters.
 
 #include <cuda_runtime.h>
 
@@ -21,12 +21,11 @@
 
 namespace {
 
-// Scratch of the step kernel: the job descriptor and the status words.
+// Scratch of the step kernel: its status and counter words.
 constexpr size_t kScratchBytes = 1024;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 struct ScratchLayout {
-  lf::JobDesc job;
   lf::DevStatus st;
 };
 static_assert(sizeof(ScratchLayout) <= kScratchBytes, "scratch too small");
@@ -96,25 +95,35 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers, cons
   if (s != LF_OK) return s;
   auto* d_layout = static_cast<ScratchLayout*>(base);
 
-  ScratchLayout h;
-  std::memset(&h, 0, sizeof(h));                 // status words start at zero, epoch 0 -> buf[0] is the input
-  h.job.n_v = n_v;
-  h.job.n_layers = n_layers;
-  h.job.num_tiles = static_cast<int32_t>(tiles);
-  h.job.tile_cap = tile_cap;
-  h.job.L_rowptr = d_L_rowptr;
-  h.job.L_colval = reinterpret_cast<const int2*>(d_L_colval);
-  h.job.buf[0] = lf::FieldBuf{const_cast<int2*>(reinterpret_cast<const int2*>(d_rows_in)),
-                              const_cast<uint16_t*>(d_ids_in), const_cast<float*>(d_vals_in)};
-  h.job.buf[1] = lf::FieldBuf{reinterpret_cast<int2*>(d_rows_out), d_ids_out, d_vals_out};
-  h.job.st = &d_layout->st;
-  h.job.c = lf::Coefs{static_cast<float>(p.dt),   static_cast<float>(p.mu),   static_cast<float>(p.w_cc),
-                      static_cast<float>(p.w_cb), static_cast<float>(p.a_cc), static_cast<float>(p.a_cb),
-                      static_cast<float>(p.e_cc), static_cast<float>(p.e_cb), static_cast<float>(p.e_bc)};
+  lf::BatchParams bp;
+  std::memset(&bp, 0, sizeof(bp));
+  bp.n_jobs = 1;
+  bp.step = 0;
+  bp.tile_start[0] = 0;
+  bp.tile_start[1] = static_cast<int32_t>(tiles);
+  lf::JobDesc& job = bp.job[0];
+  job.n_v = n_v;
+  job.n_layers = n_layers;
+  job.num_tiles = static_cast<int32_t>(tiles);
+  job.tile_cap = tile_cap;
+  job.parity0 = 0;                                // buf[0] is the input, buf[1] the output
+  job.steps = 1;
+  job.L_rowptr = d_L_rowptr;
+  job.L_colval = reinterpret_cast<const int2*>(d_L_colval);
+  job.buf[0] = lf::FieldBuf{const_cast<int2*>(reinterpret_cast<const int2*>(d_rows_in)),
+                            const_cast<uint16_t*>(d_ids_in), const_cast<float*>(d_vals_in)};
+  job.buf[1] = lf::FieldBuf{reinterpret_cast<int2*>(d_rows_out), d_ids_out, d_vals_out};
+  job.st = &d_layout->st;
+  job.c = lf::Coefs{static_cast<float>(p.dt),   static_cast<float>(p.mu),   static_cast<float>(p.w_cc),
+                    static_cast<float>(p.w_cb), static_cast<float>(p.a_cc), static_cast<float>(p.a_cb),
+                    static_cast<float>(p.e_cc), static_cast<float>(p.e_cb), static_cast<float>(p.e_bc)};
+  // the status words start at zero; nnz is the input's (known after the step)
+  lf::DevStatus h;
+  std::memset(&h, 0, sizeof(h));
 
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-  cudaError_t e = cudaMemcpyAsync(d_layout, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = lf::launch_step(&d_layout->job, static_cast<int>(tiles), LF_F32, stream);
+  cudaError_t e = cudaMemcpyAsync(&d_layout->st, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = lf::launch_step(bp, LF_F32, stream);
   lf::DevStatus st;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&st, &d_layout->st, sizeof(st), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

@@ -9,9 +9,11 @@ same number on every machine.
 from .rng import splitmix64, uniform01, uniform
 from .meshes import icosphere, planar_grid, noisy_torus, Mesh
 from .seeds import sample_seeds
+from .jobs import JobSpec, batch_mix, serve_trace, make_mesh
 
 __all__ = [
     "splitmix64", "uniform01", "uniform",
     "icosphere", "planar_grid", "noisy_torus", "Mesh",
     "sample_seeds",
+    "JobSpec", "batch_mix", "serve_trace", "make_mesh",
 ]

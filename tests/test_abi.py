@@ -104,3 +104,22 @@ def test_package_fails_loudly_without_library(tmp_path):
             "try:\n    import paper_1804_09152_gb300._lib\nexcept ImportError as e:\n    print('RAISED', e)\n")
     out = subprocess.run(["python", "-c", code], capture_output=True, text=True, cwd=ROOT)
     assert "RAISED" in out.stdout
+
+
+def test_server_and_batch_reject_invalid_input_without_gpu(lib):
+    p = lib.lf_server_default_params()
+    assert (p.hbm_budget_bytes, p.max_active, p.chunk_steps) == (150_000_000_000, 64, 256)
+    out = ctypes.c_void_p()
+    for bad in (dict(max_active=0), dict(max_active=65), dict(chunk_steps=0), dict(hbm_budget_bytes=0)):
+        sp = lib.lf_server_default_params(**bad)
+        assert lib._lib.lf_server_create(None, ctypes.byref(sp), ctypes.byref(out)) == lib.LF_ERR_INVALID, bad
+        assert lib.lf_last_error(None)
+    assert lib._lib.lf_server_create(None, None, None) == lib.LF_ERR_INVALID
+    assert lib._lib.lf_server_wait(None, 1, 0.0, None, None, 0) == lib.LF_ERR_INVALID
+    assert lib._lib.lf_server_drain(None, 0.0) == lib.LF_ERR_INVALID
+    lib._lib.lf_server_destroy(None)
+    cnt = (ctypes.c_int32 * 1)(3)
+    assert lib._lib.lf_step_batch(None, 1, cnt) == lib.LF_ERR_INVALID
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib._lib.lf_step_batch(arr, 0, cnt) == lib.LF_ERR_INVALID
+    assert lib._lib.lf_step_batch(arr, 1, cnt) == lib.LF_ERR_INVALID      # null mesh
