@@ -46,7 +46,7 @@ WORKLOADS = {
 
 # DRAM bytes of one step-kernel launch from an ncu capture of the grid512
 # workload, valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"kernel_sha": "222d53d36e4b1912", "bytes_per_launch": 18434432}
 L2_FLUSH_BYTES = 512 << 20
 
 

@@ -296,6 +296,28 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers,
  */
 lf_status lf_lloyd(lf_mesh m, int32_t rounds, int32_t steps_per_round, int32_t* seeds_out);
 
+/*
+ * Dual mesh (Sec. 5.2) of the current partition, with a vertex at each seed.
+ * A cell covers vertex v when F(v, c) >= params.iso (FP32 comparison; iso in
+ * [1/16, 1], default 0.25).  Cells are adjacent when they cover a common
+ * vertex (A_v), or when they cover vertices of a common face and their
+ * isolines (level iso, linear on the face) cross there and they do not
+ * already share two A_v neighbours (the manifold check).  Every three
+ * mutually adjacent cells form a triangle, except the triangle of the three
+ * neighbours of a cell that has exactly three mutually adjacent neighbours
+ * (a spurious triangle).  Triangles are oriented consistently, breadth-first
+ * over shared edges, starting from the first triangle of each connected part
+ * oriented along the mesh normals at its seeds.  The mesh passes run on the
+ * device; the graph stage over the k cells runs on the host.
+ * tris (nullable) receives *n_tris rows of 3 seed vertex ids, in sorted order
+ * of their vertex sets; with tris NULL only *n_tris is set.  The result is
+ * kept until the field changes, so a size query followed by the copy costs
+ * one extraction.  Errors: LF_ERR_INVALID (null n_tris, iso out of range),
+ * LF_ERR_STATE (no field, no geometry, unknown seeds), LF_ERR_CAPACITY (cap
+ * smaller than *n_tris, which is still set), LF_ERR_OOM, LF_ERR_CUDA.
+ */
+lf_status lf_extract_dual(lf_mesh m, int32_t* tris, int64_t cap, int64_t* n_tris);
+
 /* ------------------------------------------------------------------------
  * Serving form: continuous batching of tessellation jobs.
  *

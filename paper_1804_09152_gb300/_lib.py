@@ -114,6 +114,8 @@ _lib.lf_step_batch.restype = ctypes.c_int
 _lib.lf_step_noalloc.argtypes = [_P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _i32, ctypes.POINTER(lf_params),
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
 _lib.lf_step_noalloc.restype = ctypes.c_int
+_lib.lf_extract_dual.argtypes = [_P, _P, _i64, ctypes.POINTER(_i64)]
+_lib.lf_extract_dual.restype = ctypes.c_int
 _lib.lf_lloyd.argtypes = [_P, _i32, _i32, _P]
 _lib.lf_lloyd.restype = ctypes.c_int
 _lib.lf_server_default_params.argtypes = [ctypes.POINTER(lf_server_params)]
@@ -134,7 +136,7 @@ _lib.lf_server_destroy.restype = None
 
 EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_step", "lf_labels",
             "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
-            "lf_step_noalloc", "lf_step_batch", "lf_lloyd", "lf_server_default_params", "lf_server_create",
+            "lf_step_noalloc", "lf_step_batch", "lf_lloyd", "lf_extract_dual", "lf_server_default_params", "lf_server_create",
             "lf_server_submit", "lf_server_wait", "lf_server_drain", "lf_server_stats", "lf_server_destroy"]
 
 
@@ -241,6 +243,15 @@ def lf_lloyd(mesh, rounds, steps_per_round, k):
     return out
 
 
+def lf_extract_dual(mesh):
+    """Oriented dual triangles over seed vertex ids, (n, 3) int32."""
+    n = _i64()
+    _check(_lib.lf_extract_dual(mesh, None, 0, ctypes.byref(n)), mesh)
+    out = np.empty((n.value, 3), np.int32)
+    _check(_lib.lf_extract_dual(mesh, _ptr(out), n.value, ctypes.byref(n)), mesh)
+    return out
+
+
 def lf_labels(mesh, n_v, with_max=False):
     lab = np.empty(n_v, np.int32)
     mx = np.empty(n_v, np.float32) if with_max else None
@@ -325,6 +336,9 @@ class Mesh:
 
     def labels(self, with_max=False):
         return lf_labels(self.h, self.n_v, with_max)
+
+    def extract_dual(self):
+        return lf_extract_dual(self.h)
 
     def lloyd(self, rounds, steps_per_round):
         return lf_lloyd(self.h, rounds, steps_per_round, self.stats()["n_layers"] - 1)

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <deque>
+#include <unordered_map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -68,6 +71,13 @@ struct lf_mesh_s {
   int32_t* d_seed_new = nullptr;
   lf::LloydScratch lloyd{};
   int64_t lloyd_k = 0;
+  // dual-mesh extraction: device scratch and the last result
+  lf::DualScratch dual{};
+  int64_t dual_k = 0;
+  int32_t* d_dual_seeds = nullptr;
+  int64_t version = 0;           // bumped whenever the field is replaced (lf_seed, lf_set_field)
+  int64_t dual_version = -1, dual_steps = -1;
+  std::vector<int32_t> dual_tris;
 
   ~lf_mesh_s() {
     cudaStreamSynchronize(stream);
@@ -595,6 +605,7 @@ lf_status lf_seed(lf_mesh m, const int32_t* seeds, int32_t k) {
   m->steps = 0;
   m->retries = 0;
   m->seeds.assign(seeds, seeds + k);
+  ++m->version;
   return LF_OK;
 }
 
@@ -905,9 +916,232 @@ lf_status lf_set_field(lf_mesh m, const int64_t* rowptr, const int32_t* layer, c
   m->h_job.n_layers = n_layers;
   m->h_st.nnz = static_cast<unsigned long long>(nnz);
   if (static_cast<int64_t>(m->seeds.size()) != n_layers - 1) m->seeds.clear();
+  ++m->version;
   s = upload_job(m);
   if (s == LF_OK) s = upload_status(m);
   return s;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Graph stage of the dual extraction (Sec. 5.2) on k cells: the manifold check
+// (a face-only pair is dropped when its cells share two or more neighbours of
+// A_v), the triangles (mutually adjacent triples), the removal of spurious
+// triangles (the three neighbours of a cell with exactly three mutually
+// adjacent neighbours) and the orientation (breadth-first over shared edges
+// from the first triangle of each part, oriented along the mesh normals at
+// its seeds).  Returns oriented cell triples in sorted order of their sets.
+std::vector<std::array<int32_t, 3>> dual_graph(int k, const std::vector<uint32_t>& av,
+                                               const std::vector<uint32_t>& cand, const std::vector<double>& pos,
+                                               const std::vector<double>& nrm) {
+  std::vector<std::vector<int32_t>> Nv(static_cast<size_t>(k));
+  for (uint32_t key : av) {
+    const int32_t c = static_cast<int32_t>(key >> 16), d = static_cast<int32_t>(key & 0xffffu);
+    Nv[static_cast<size_t>(c)].push_back(d);
+    Nv[static_cast<size_t>(d)].push_back(c);
+  }
+  for (auto& x : Nv) std::sort(x.begin(), x.end());
+  auto shared = [](const std::vector<int32_t>& a, const std::vector<int32_t>& b) {
+    size_t i = 0, j = 0, n = 0;
+    while (i < a.size() && j < b.size()) {
+      if (a[i] == b[j]) { ++n; ++i; ++j; }
+      else if (a[i] < b[j]) ++i;
+      else ++j;
+    }
+    return n;
+  };
+  std::vector<std::vector<int32_t>> N = Nv;
+  for (uint32_t key : cand) {
+    const int32_t c = static_cast<int32_t>(key >> 16), d = static_cast<int32_t>(key & 0xffffu);
+    if (shared(Nv[static_cast<size_t>(c)], Nv[static_cast<size_t>(d)]) >= 2) continue;
+    N[static_cast<size_t>(c)].push_back(d);
+    N[static_cast<size_t>(d)].push_back(c);
+  }
+  for (auto& x : N) {
+    std::sort(x.begin(), x.end());
+    x.erase(std::unique(x.begin(), x.end()), x.end());
+  }
+  std::vector<std::array<int32_t, 3>> tri;
+  for (int32_t i = 0; i < k; ++i) {
+    const auto& Ni = N[static_cast<size_t>(i)];
+    for (int32_t j : Ni) {
+      if (j <= i) continue;
+      const auto& Nj = N[static_cast<size_t>(j)];
+      size_t a = 0, b = 0;
+      while (a < Ni.size() && b < Nj.size()) {
+        if (Ni[a] == Nj[b]) {
+          if (Ni[a] > j) tri.push_back({i, j, Ni[a]});
+          ++a;
+          ++b;
+        } else if (Ni[a] < Nj[b]) {
+          ++a;
+        } else {
+          ++b;
+        }
+      }
+    }
+  }
+  std::sort(tri.begin(), tri.end());
+  std::vector<char> spurious(tri.size(), 0);
+  for (int32_t i = 0; i < k; ++i) {
+    const auto& Ni = N[static_cast<size_t>(i)];
+    if (Ni.size() != 3) continue;
+    const std::array<int32_t, 3> t3 = {Ni[0], Ni[1], Ni[2]};
+    auto it = std::lower_bound(tri.begin(), tri.end(), t3);
+    if (it != tri.end() && *it == t3) spurious[static_cast<size_t>(it - tri.begin())] = 1;
+  }
+  std::vector<std::array<int32_t, 3>> kept;
+  for (size_t t = 0; t < tri.size(); ++t)
+    if (!spurious[t]) kept.push_back(tri[t]);
+  // orientation
+  std::unordered_map<uint64_t, std::vector<int32_t>> edge_tris;
+  auto ekey = [](int32_t u, int32_t v) {
+    return (static_cast<uint64_t>(std::min(u, v)) << 32) | static_cast<uint32_t>(std::max(u, v));
+  };
+  for (size_t t = 0; t < kept.size(); ++t) {
+    const auto& x = kept[t];
+    edge_tris[ekey(x[0], x[1])].push_back(static_cast<int32_t>(t));
+    edge_tris[ekey(x[1], x[2])].push_back(static_cast<int32_t>(t));
+    edge_tris[ekey(x[0], x[2])].push_back(static_cast<int32_t>(t));
+  }
+  std::vector<std::array<int32_t, 3>> out(kept.size());
+  std::vector<char> done(kept.size(), 0);
+  std::deque<int32_t> q;
+  for (size_t start = 0; start < kept.size(); ++start) {
+    if (done[start]) continue;
+    const int32_t a = kept[start][0], b = kept[start][1], c = kept[start][2];
+    const double* pa = &pos[3 * static_cast<size_t>(a)];
+    const double* pb = &pos[3 * static_cast<size_t>(b)];
+    const double* pc = &pos[3 * static_cast<size_t>(c)];
+    const double u[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+    const double w[3] = {pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2]};
+    const double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+    double sdot = 0.0;
+    for (int j = 0; j < 3; ++j)
+      sdot += n[j] * (nrm[3 * static_cast<size_t>(a) + j] + nrm[3 * static_cast<size_t>(b) + j] +
+                      nrm[3 * static_cast<size_t>(c) + j]);
+    out[start] = sdot >= 0.0 ? std::array<int32_t, 3>{a, b, c} : std::array<int32_t, 3>{a, c, b};
+    done[start] = 1;
+    q.push_back(static_cast<int32_t>(start));
+    while (!q.empty()) {
+      const int32_t ti = q.front();
+      q.pop_front();
+      const auto o = out[static_cast<size_t>(ti)];
+      const int32_t de[3][2] = {{o[0], o[1]}, {o[1], o[2]}, {o[2], o[0]}};
+      for (const auto& e : de) {
+        for (int32_t tj : edge_tris[ekey(e[0], e[1])]) {
+          if (done[static_cast<size_t>(tj)]) continue;
+          const auto& x = kept[static_cast<size_t>(tj)];
+          // the neighbour runs e[1] -> e[0]
+          const bool fwd = (x[0] == e[1] && x[1] == e[0]) || (x[1] == e[1] && x[2] == e[0]) ||
+                           (x[2] == e[1] && x[0] == e[0]);
+          out[static_cast<size_t>(tj)] = fwd ? x : std::array<int32_t, 3>{x[0], x[2], x[1]};
+          done[static_cast<size_t>(tj)] = 1;
+          q.push_back(tj);
+        }
+      }
+    }
+  }
+  return out;
+}
+
+uint32_t next_pow2(uint64_t x) {
+  uint32_t p = 1;
+  while (p < x && p < (1u << 31)) p <<= 1;
+  return p;
+}
+
+lf_status dual_scratch(lf_mesh m, int64_t k, uint32_t cap) {
+  if (m->dual_k == k && m->dual.cap >= cap) return LF_OK;
+  for (void* p : {static_cast<void*>(m->dual.Hv), static_cast<void*>(m->dual.Hc), static_cast<void*>(m->dual.out_v),
+                  static_cast<void*>(m->dual.out_c), static_cast<void*>(m->dual.counters),
+                  static_cast<void*>(m->dual.cell_of), static_cast<void*>(m->dual.nrm),
+                  static_cast<void*>(m->dual.pos), static_cast<void*>(m->d_dual_seeds)})
+    m->dfree(p);
+  m->dual = lf::DualScratch{};
+  m->d_dual_seeds = nullptr;
+  m->dual_k = 0;
+  m->dual.cap = cap;
+  m->dual.Hv = static_cast<uint32_t*>(m->dalloc(sizeof(uint32_t) * cap));
+  m->dual.Hc = static_cast<uint32_t*>(m->dalloc(sizeof(uint32_t) * cap));
+  m->dual.out_v = static_cast<uint32_t*>(m->dalloc(sizeof(uint32_t) * cap));
+  m->dual.out_c = static_cast<uint32_t*>(m->dalloc(sizeof(uint32_t) * cap));
+  m->dual.counters = static_cast<uint32_t*>(m->dalloc(sizeof(uint32_t) * 4));
+  m->dual.cell_of = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * m->n_v));
+  m->dual.nrm = static_cast<double*>(m->dalloc(sizeof(double) * 3 * k));
+  m->dual.pos = static_cast<double*>(m->dalloc(sizeof(double) * 3 * k));
+  m->d_dual_seeds = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * k));
+  if (!m->dual.Hv || !m->dual.Hc || !m->dual.out_v || !m->dual.out_c || !m->dual.counters || !m->dual.cell_of ||
+      !m->dual.nrm || !m->dual.pos || !m->d_dual_seeds)
+    return fail(m, LF_ERR_OOM, "dual-mesh scratch");
+  m->dual_k = k;
+  return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lf_status lf_extract_dual(lf_mesh m, int32_t* tris, int64_t cap, int64_t* n_tris) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (!n_tris) return fail(m, LF_ERR_INVALID, "n_tris must not be NULL");
+  if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed must come first");
+  if (!m->d_V) return fail(m, LF_ERR_STATE, "the dual mesh needs a mesh made by lf_create_mesh");
+  const int64_t k = m->n_layers - 1;
+  if (static_cast<int64_t>(m->seeds.size()) != k)
+    return fail(m, LF_ERR_STATE, "the seeds of the current field are unknown (lf_seed sets them)");
+  const double iso = m->params.iso;
+  if (!(iso >= 1.0 / 16.0 && iso <= 1.0)) return fail(m, LF_ERR_INVALID, "iso must lie in [1/16, 1]");
+  if (m->dual_version != m->version || m->dual_steps != m->steps) {
+    s = read_status(m);
+    if (s != LF_OK) return s;
+    const int cur = static_cast<int>(m->h_st.epoch & 1u);
+    uint32_t tab = next_pow2(std::max<uint64_t>(4096, 16 * static_cast<uint64_t>(k)));
+    uint32_t counters[4] = {0, 0, 0, 0};
+    for (int attempt = 0;; ++attempt) {
+      s = dual_scratch(m, k, tab);
+      if (s != LF_OK) return s;
+      LF_CUDA(m, cudaMemcpyAsync(m->d_dual_seeds, m->seeds.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice,
+                                 m->stream));
+      LF_CUDA(m, lf::launch_dual(m->h_job, cur, m->dtype, m->d_V, m->d_tri, static_cast<int>(m->n_f),
+                                 static_cast<int>(k), static_cast<float>(iso), m->d_dual_seeds, m->dual, m->stream));
+      LF_CUDA(m, cudaMemcpyAsync(counters, m->dual.counters, sizeof(counters), cudaMemcpyDeviceToHost, m->stream));
+      LF_CUDA(m, cudaStreamSynchronize(m->stream));
+      if (counters[0] == 0u) break;
+      if (attempt >= 6 || tab >= (1u << 30)) return fail(m, LF_ERR_CAPACITY, "too many cell pairs");
+      tab *= 4;                                   // a set ran full: larger tables, again
+    }
+    std::vector<uint32_t> av(counters[1]), cand(counters[2]);
+    std::vector<double> pos(3 * static_cast<size_t>(k)), nrm(3 * static_cast<size_t>(k));
+    if (!av.empty())
+      LF_CUDA(m, cudaMemcpyAsync(av.data(), m->dual.out_v, sizeof(uint32_t) * av.size(), cudaMemcpyDeviceToHost,
+                                 m->stream));
+    if (!cand.empty())
+      LF_CUDA(m, cudaMemcpyAsync(cand.data(), m->dual.out_c, sizeof(uint32_t) * cand.size(),
+                                 cudaMemcpyDeviceToHost, m->stream));
+    LF_CUDA(m, cudaMemcpyAsync(pos.data(), m->dual.pos, sizeof(double) * pos.size(), cudaMemcpyDeviceToHost,
+                               m->stream));
+    LF_CUDA(m, cudaMemcpyAsync(nrm.data(), m->dual.nrm, sizeof(double) * nrm.size(), cudaMemcpyDeviceToHost,
+                               m->stream));
+    LF_CUDA(m, cudaStreamSynchronize(m->stream));
+    std::sort(av.begin(), av.end());
+    std::sort(cand.begin(), cand.end());
+    const auto t3 = dual_graph(static_cast<int>(k), av, cand, pos, nrm);
+    m->dual_tris.resize(3 * t3.size());
+    for (size_t t = 0; t < t3.size(); ++t)
+      for (int j = 0; j < 3; ++j) m->dual_tris[3 * t + j] = m->seeds[static_cast<size_t>(t3[t][j])];
+    m->dual_version = m->version;
+    m->dual_steps = m->steps;
+  }
+  const int64_t n = static_cast<int64_t>(m->dual_tris.size() / 3);
+  *n_tris = n;
+  if (!tris) return LF_OK;
+  if (cap < n) return fail(m, LF_ERR_CAPACITY, "tris holds fewer than *n_tris triangles");
+  if (n > 0) std::memcpy(tris, m->dual_tris.data(), sizeof(int32_t) * 3 * n);
+  return LF_OK;
 }
 
 lf_status lf_lloyd(lf_mesh m, int32_t rounds, int32_t steps_per_round, int32_t* seeds_out) {

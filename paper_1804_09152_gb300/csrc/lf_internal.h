@@ -119,6 +119,22 @@ cudaError_t launch_lloyd(const JobDesc& job, int buf, const double* V, const int
 // Message returned by lf_last_error(NULL) (thread-local).
 void set_last_error(const std::string& msg);
 
+// Device scratch of one dual-mesh extraction (k cells, n_v vertices).
+struct DualScratch {
+  uint32_t* Hv;         // cap: hash set of the pairs covering a common vertex
+  uint32_t* Hc;         // cap: hash set of the face-only pairs whose isolines cross
+  uint32_t cap;         // power of two
+  uint32_t* out_v;      // cap: compacted Hv
+  uint32_t* out_c;      // cap: compacted Hc
+  uint32_t* counters;   // 4: overflow, |out_v|, |out_c|, unused
+  int32_t* cell_of;     // n_v: cell whose seed a vertex is, or -1
+  double* nrm;          // k * 3: mesh normal (area weighted) at each seed vertex
+  double* pos;          // k * 3: seed positions
+};
+// Mesh passes of the dual extraction (Sec. 5.2) on the field in job.buf[buf].
+cudaError_t launch_dual(const JobDesc& job, int buf, int dtype, const double* V, const int32_t* tri, int n_f, int k,
+                        float iso, const int32_t* d_seeds, DualScratch sc, cudaStream_t s);
+
 // Host helpers shared with the serving runtime (lf_server.cpp).
 // Cotangent operator of a triangle mesh as off-diagonal FP64 CSR; false (with
 // a reason) on a zero-area face.

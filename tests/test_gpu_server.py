@@ -68,9 +68,10 @@ def test_server_matches_jobs_alone(lf):
         assert st["skeleton_total"] == total
 
 
-def test_server_admits_under_the_memory_budget(lf):
+def test_server_admits_under_the_memory_budget(lf, oracle_mod):
     m = synth.planar_grid(61, seed=2)
-    with lf.Mesh(m.V, m.F) as probe:
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    with lf.Mesh(csr=(L.rowptr, L.col, L.val)) as probe:      # a server job holds no geometry
         one = probe.stats()["device_bytes"]
     big = synth.planar_grid(200, seed=2)
     # room for one grid61 job at a time (its estimate is its device bytes
