@@ -114,6 +114,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(dist, seconds, units, device):
+    """Whole-job figures over all ranks: the slowest rank's time and the units
+    every rank processed (independent jobs per rank, so no other exchange)."""
+    if dist is None:
+        return seconds, float(units)
+    import torch
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def oracle_sample(wl, n_steps):
     """The FP64 oracle on the first n_steps time steps of the job."""
     import oracle
@@ -221,14 +234,7 @@ def run_ours(args, wl):
         st = mesh.stats()
 
     t_job = sum(job_ms) / 1e3
-    if dist:
-        t = torch.tensor([t_job], device="cuda")
-        u = torch.tensor([float(units)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        t_all, units_all = float(t.item()), float(u.item())
-    else:
-        t_all, units_all = t_job, float(units)
+    t_all, units_all = aggregate(dist, t_job, units, "cuda")
     value = units_all / t_all
 
     # roofline of the step kernel: algorithmic bytes (ideal reuse) per launch
@@ -399,6 +405,74 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lloyd(args):
+    """C2 with the paper's full pipeline (Sec. 5): 2000 steps, then Lloyd-like
+    rounds (seed update + 2000 steps each), then the dual mesh (Sec. 5.2)."""
+    import torch
+    import paper_1804_09152_gb300 as pkg
+    pkg.build()
+    from paper_1804_09152_gb300 import _lib as lf
+
+    wl = WORKLOADS["grid512"]
+    m = wl["mesh"]()
+    seeds = synth.sample_seeds(m.n_v, wl["k"], wl["seed_stream"])
+    T, R = wl["steps"], args.lloyd_rounds
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        mesh = lf.Mesh(m.V, m.F, device=lf.torch_device(stream))
+
+        def ev():
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            return e
+
+        def pipeline():
+            mesh.seed(seeds)
+            e0 = ev()
+            mesh.step(T)
+            units = mesh.stats()["skeleton_total"]
+            upd_ms = 0.0
+            for _ in range(R):
+                a = ev()
+                mesh.lloyd(1, 0)                  # the seed update alone
+                b = ev()
+                mesh.step(T)
+                b.synchronize()
+                upd_ms += a.elapsed_time(b)
+                units += mesh.stats()["skeleton_total"]
+            c = ev()
+            tri = mesh.extract_dual()
+            d = ev()
+            d.synchronize()
+            return e0.elapsed_time(d), upd_ms / max(R, 1), c.elapsed_time(d), units, len(tri)
+
+        for _ in range(args.warmup):
+            pipeline()
+        res = []
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                res.append(pipeline())
+        mesh.close()
+    total_ms = sum(r[0] for r in res)
+    units = sum(r[3] for r in res)
+    line = {
+        "metric": METRIC, "value": units / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / len(res), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "grid512_lloyd", "desc": wl["desc"] + f", then {R} Lloyd-like rounds of {T} steps "
+                   "and the dual mesh", "lloyd_rounds": R, "time_steps_per_round": T,
+                   "l2": "flushed before each pipeline (512 MiB write)"},
+        "lloyd_update_ms": statistics.mean(r[1] for r in res),
+        "dual_extraction_ms": statistics.mean(r[2] for r in res),
+        "dual_triangles": res[-1][4],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving form: a prefix of the Poisson trace (200 jobs/s; n_v log-normal
     in [5k, 2M]; icosphere / torus / grid; 16-8192 seeds; 500-3000 steps)
@@ -472,7 +546,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch64", "serve"], default="grid512")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch64", "serve", "grid512_lloyd"],
+                    default="grid512")
+    ap.add_argument("--lloyd-rounds", type=int, default=10)
+    ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default=None,
+                    help="storage type of the field values (mesh workloads; default: the workload's)")
     ap.add_argument("--serve-jobs", type=int, default=100)
     ap.add_argument("--cpu-sample-steps", type=int, default=200)
     ap.add_argument("--ref-sample-steps", type=int, default=40)
@@ -482,7 +560,12 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
-    wl = WORKLOADS[args.workload]
+    if args.workload == "grid512_lloyd":
+        return run_lloyd(args)
+    wl = dict(WORKLOADS[args.workload])
+    if args.dtype:
+        wl["dtype"] = args.dtype
+        wl["desc"] = wl["desc"].replace("FP32 field", f"{args.dtype.upper()} field storage, FP32 arithmetic")
     if args.impl == "reference":
         run_reference(args, wl)
     else:
