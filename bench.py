@@ -46,7 +46,7 @@ WORKLOADS = {
 
 # DRAM bytes of one step-kernel launch from an ncu capture of the grid512
 # workload, valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"kernel_sha": "222d53d36e4b1912", "bytes_per_launch": 18434432}
+NCU_TRAFFIC = {"kernel_sha": "fe4e47e7a1f88d7c", "bytes_per_launch": 17866325}
 L2_FLUSH_BYTES = 512 << 20
 
 

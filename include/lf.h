@@ -254,7 +254,10 @@ const char* lf_last_error(lf_mesh m);
  *   8-byte aligned; the rows of tile t lie one after another, layer ids
  *   ascending within a row, inside entries [t * tile_cap, (t + 1) * tile_cap)
  *   of d_ids_* (uint16) and d_vals_* (float); both fields hold T * tile_cap
- *   entries.  n_layers = k + 1 (the base layer is k).
+ *   entries.  d_head_* hold 4 int32 per vertex (16-byte aligned): the row's
+ *   count, id0 | id1 << 16, and the IEEE-754 bits of its first two values
+ *   (zeros where the row is shorter) -- the input's must match its rows, the
+ *   output's is written.  n_layers = k + 1 (the base layer is k).
  *   nnz_out (host, nullable): entries of the output field.
  *   need_tile_cap (host, nullable): on LF_ERR_CAPACITY, the tile_cap needed.
  * Limits: tile_cap a multiple of 16 and >= 256; n_v <= 2^31 - 257;
@@ -269,9 +272,9 @@ const char* lf_last_error(lf_mesh m);
  */
 lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers,
                           const int32_t* d_L_rowptr, const int32_t* d_L_colval,
-                          const int32_t* d_rows_in, const uint16_t* d_ids_in, const float* d_vals_in,
-                          int32_t* d_rows_out, uint16_t* d_ids_out, float* d_vals_out,
-                          int32_t tile_cap, const lf_params* params,
+                          const int32_t* d_rows_in, const int32_t* d_head_in, const uint16_t* d_ids_in,
+                          const float* d_vals_in, int32_t* d_rows_out, int32_t* d_head_out,
+                          uint16_t* d_ids_out, float* d_vals_out, int32_t tile_cap, const lf_params* params,
                           int64_t* nnz_out, int64_t* need_tile_cap);
 
 /*

@@ -111,8 +111,8 @@ _lib.lf_last_error.argtypes = [_P]
 _lib.lf_last_error.restype = ctypes.c_char_p
 _lib.lf_step_batch.argtypes = [ctypes.POINTER(_P), _i32, ctypes.POINTER(_i32)]
 _lib.lf_step_batch.restype = ctypes.c_int
-_lib.lf_step_noalloc.argtypes = [_P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _i32, ctypes.POINTER(lf_params),
-                                 ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+_lib.lf_step_noalloc.argtypes = [_P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _i32,
+                                 ctypes.POINTER(lf_params), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
 _lib.lf_step_noalloc.restype = ctypes.c_int
 _lib.lf_extract_dual.argtypes = [_P, _P, _i64, ctypes.POINTER(_i64)]
 _lib.lf_extract_dual.restype = ctypes.c_int
@@ -287,16 +287,17 @@ def lf_destroy_mesh(mesh):
     _lib.lf_destroy_mesh(mesh)
 
 
-def lf_step_noalloc(stream, n_v, n_layers, L_rowptr, L_colval, rows_in, ids_in, vals_in, rows_out, ids_out,
-                    vals_out, tile_cap, params=None):
+def lf_step_noalloc(stream, n_v, n_layers, L_rowptr, L_colval, rows_in, head_in, ids_in, vals_in, rows_out,
+                    head_out, ids_out, vals_out, tile_cap, params=None):
     """One step on caller-owned device buffers (integer device addresses).
 
     Returns (nnz_out, need_tile_cap); raises LFError on failure.
     """
     nnz = _i64(0)
     need = _i64(0)
-    st = _lib.lf_step_noalloc(stream, n_v, n_layers, L_rowptr, L_colval, rows_in, ids_in, vals_in, rows_out,
-                              ids_out, vals_out, tile_cap, ctypes.byref(params) if params is not None else None,
+    st = _lib.lf_step_noalloc(stream, n_v, n_layers, L_rowptr, L_colval, rows_in, head_in, ids_in, vals_in,
+                              rows_out, head_out, ids_out, vals_out, tile_cap,
+                              ctypes.byref(params) if params is not None else None,
                               ctypes.byref(nnz), ctypes.byref(need))
     if st != LF_OK:
         err = LFError(st, _lib.lf_last_error(None).decode(errors="replace"))

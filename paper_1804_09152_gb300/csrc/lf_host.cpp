@@ -389,8 +389,12 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
   m->d_Lrp = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * (n_v + 1)));
   m->d_Lcv = static_cast<int2*>(m->dalloc(sizeof(int2) * std::max<int64_t>(nnz, 1)));
   m->d_st = static_cast<lf::DevStatus*>(m->dalloc(sizeof(lf::DevStatus)));
-  for (int b = 0; b < 2; ++b) m->buf[b].rows = static_cast<int2*>(m->dalloc(sizeof(int2) * n_v));
-  if (!m->d_Lrp || !m->d_Lcv || !m->d_st || !m->buf[0].rows || !m->buf[1].rows) {
+  for (int b = 0; b < 2; ++b) {
+    m->buf[b].rows = static_cast<int2*>(m->dalloc(sizeof(int2) * n_v));
+    m->buf[b].head = static_cast<int4*>(m->dalloc(sizeof(int4) * n_v));
+  }
+  if (!m->d_Lrp || !m->d_Lcv || !m->d_st || !m->buf[0].rows || !m->buf[1].rows || !m->buf[0].head ||
+      !m->buf[1].head) {
     delete m;
     return fail(nullptr, LF_ERR_OOM, "device allocation");
   }
@@ -490,6 +494,7 @@ int64_t device_bytes_estimate(int64_t n_v, int64_t nnz_off, const lf_params& prm
                                                : 3 * kTile;
   const int64_t entries = tiles * cap;
   return r(4 * (n_v + 1)) + r(8 * nnz_off) + r(static_cast<int64_t>(sizeof(DevStatus))) + 2 * r(8 * n_v) +
+         2 * r(16 * n_v) /* head records */ +
          2 * (r(2 * entries) + r(value_bytes(prm.field_dtype) * entries)) + r(4 * n_v) /* labels */;
 }
 }  // namespace lf
@@ -912,6 +917,7 @@ lf_status lf_set_field(lf_mesh m, const int64_t* rowptr, const int32_t* layer, c
                                m->stream));
     LF_CUDA(m, lf::launch_narrow(m->d_scratch_f, m->buf[cur].vals, entries, m->dtype, m->stream));
   }
+  LF_CUDA(m, lf::launch_build_head(m->buf[cur], static_cast<int>(m->n_v), m->dtype, m->stream));
   m->n_layers = n_layers;
   m->h_job.n_layers = n_layers;
   m->h_st.nnz = static_cast<unsigned long long>(nnz);

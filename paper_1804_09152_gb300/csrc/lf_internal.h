@@ -39,9 +39,14 @@ static_assert(sizeof(DevStatus) == 72, "DevStatus layout");
 // One copy of the field in tile-segmented CSR.  Vertex i belongs to tile
 // i / kTile; the rows of a tile are stored one after another, ids ascending
 // within a row, in the segment [tile * tile_cap, (tile + 1) * tile_cap) of ids
-// and vals.  rows[i] = (start, count) of row i.
+// and vals.  rows[i] = (start, count) of row i.  head[i] repeats the count
+// and the first two entries of row i in one 16-byte record -- (count,
+// id0 | id1 << 16, value bits of entry 0, value bits of entry 1), values in
+// the storage type's bits, unused parts zero -- so the step kernel reads a
+// neighbour's row of one or two entries with a single load.
 struct FieldBuf {
   int2* rows;        // n_v
+  int4* head;        // n_v
   uint16_t* ids;     // num_tiles * tile_cap
   void* vals;        // num_tiles * tile_cap values of the storage type
 };
@@ -93,6 +98,8 @@ cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_seed(const JobDesc& job, int k, const int32_t* d_seeds, int dtype, cudaStream_t s);
 cudaError_t launch_labels(const JobDesc& job, int buf, int dtype, int32_t* d_labels, float* d_maxval,
                           cudaStream_t s);
+// head[] of a field buffer from its rows, ids and vals.
+cudaError_t launch_build_head(const FieldBuf& b, int n_v, int dtype, cudaStream_t s);
 // Copies the rows of `from` into the segments of `to` (tile_cap may differ).
 cudaError_t launch_relayout(const int2* rows_from, const uint16_t* ids_from, const void* vals_from,
                             int cap_from, int2* rows_to, uint16_t* ids_to, void* vals_to, int cap_to,

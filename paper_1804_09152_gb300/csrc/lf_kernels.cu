@@ -32,23 +32,33 @@ namespace {
 // storage types
 // ---------------------------------------------------------------------------
 template <int DT> struct Val;
+// bits() / from_bits(): a stored value as the 32-bit word kept in a row's head
+// record (16-bit types in the low half).
 template <> struct Val<0> {
   using T = float;
   static __device__ __forceinline__ float load(const T* p) { return __ldg(p); }
   static __device__ __forceinline__ T round(float v) { return v; }
   static __device__ __forceinline__ float widen(T v) { return v; }
+  static __device__ __forceinline__ int bits(T v) { return __float_as_int(v); }
+  static __device__ __forceinline__ float from_bits(int b) { return __int_as_float(b); }
 };
 template <> struct Val<1> {
   using T = __nv_bfloat16;
   static __device__ __forceinline__ float load(const T* p) { return __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ T round(float v) { return __float2bfloat16_rn(v); }
   static __device__ __forceinline__ float widen(T v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ int bits(T v) { return static_cast<int>(__bfloat16_as_ushort(v)); }
+  static __device__ __forceinline__ float from_bits(int b) { return __int_as_float(b << 16); }
 };
 template <> struct Val<2> {
   using T = __half;
   static __device__ __forceinline__ float load(const T* p) { return __half2float(__ldg(p)); }
   static __device__ __forceinline__ T round(float v) { return __float2half_rn(v); }
   static __device__ __forceinline__ float widen(T v) { return __half2float(v); }
+  static __device__ __forceinline__ int bits(T v) { return static_cast<int>(__half_as_ushort(v)); }
+  static __device__ __forceinline__ float from_bits(int b) {
+    return __half2float(__ushort_as_half(static_cast<unsigned short>(b)));
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -333,13 +343,23 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
   // the first loads do not depend on the error word: issue them before the
   // barrier that publishes it
   const int i = tile * kBlock + t;
+  int4 h_own = make_int4(0, 0, 0, 0);    // head record of the own row
   if (i < n_v) {
-    const int2 ri = __ldg(nb.rows + i);
-    nb.p0 = ri.x;
-    nb.p1 = ri.x + ri.y;
+    h_own = __ldg(in.head + i);
     nb.q0 = __ldg(J.L_rowptr + i);
     nb.q1 = __ldg(J.L_rowptr + i + 1);
   }
+  // the own row's place in the segment, read only where its entries beyond
+  // the head record are needed (rows of three or more, the other tiers)
+  bool own_row_read = false;
+  auto read_own_row = [&]() {
+    if (!own_row_read && i < n_v) {
+      const int2 ri = __ldg(nb.rows + i);
+      nb.p0 = ri.x;
+      nb.p1 = ri.x + ri.y;
+    }
+    own_row_read = true;
+  };
   if (t == 0) {
     s_err = ld_relaxed_u32(&st->err);
     s_pool = 0;
@@ -352,7 +372,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
   int mode = kFast;
   bool zero_sum = false;
   int kept = 0, nsk = 0;
-  const int own = nb.p1 - nb.p0;
+  const int own = h_own.x;
   float vnew[kSlots];
   bool keep[kSlots];
 #pragma unroll
@@ -367,7 +387,18 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
   if (i < n_v) {
     if (own > kSlots) {
       mode = kMedium;
+    } else if (own <= 2) {
+      if (own > 0) {
+        mp.id[0] = h_own.y & 0xffff;
+        mp.f[0] = V::from_bits(h_own.z);
+      }
+      if (own > 1) {
+        mp.id[1] = (h_own.y >> 16) & 0xffff;
+        mp.f[1] = V::from_bits(h_own.w);
+      }
+      mp.cnt = own;
     } else {
+      read_own_row();
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
         if (s < own) {
@@ -392,15 +423,16 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
           lij[k] = __int_as_float(cv.y);
         }
       }
+      // head records of the batch's rows: count and first two entries
+      int4 hj[kChunk];
 #pragma unroll
       for (int k = 0; k < kChunk; ++k) {
-        r0[k] = rn[k] = 0;
+        hj[k] = make_int4(0, 0, 0, 0);
         if (jj[k] >= 0) {
-          const int2 rj = __ldg(nb.rows + jj[k]);
-          r0[k] = rj.x;
-          rn[k] = rj.y;
+          hj[k] = __ldg(in.head + jj[k]);
           nb.dsum += lij[k];
         }
+        rn[k] = hj[k].x;
       }
       if (mode != kFast) continue;
       // the first two entries of each row of the batch; -2 marks "no entry"
@@ -412,12 +444,12 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
         eid[2 * k] = eid[2 * k + 1] = -2;
         ex[2 * k] = ex[2 * k + 1] = 0.0f;
         if (rn[k] > 0) {
-          eid[2 * k] = __ldg(nb.Fid + r0[k]);
-          ex[2 * k] = __fmul_rn(lij[k], V::load(nb.Fval + r0[k]));
+          eid[2 * k] = hj[k].y & 0xffff;
+          ex[2 * k] = __fmul_rn(lij[k], V::from_bits(hj[k].z));
         }
         if (rn[k] > 1) {
-          eid[2 * k + 1] = __ldg(nb.Fid + r0[k] + 1);
-          ex[2 * k + 1] = __fmul_rn(lij[k], V::load(nb.Fval + r0[k] + 1));
+          eid[2 * k + 1] = (hj[k].y >> 16) & 0xffff;
+          ex[2 * k + 1] = __fmul_rn(lij[k], V::from_bits(hj[k].w));
         }
       }
       // entries whose layer already has a slot: slot x entry compare matrix,
@@ -443,15 +475,20 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
         for (int e = 0; e < kE; ++e)
           if (!hit[e] && mode == kFast && !mp.add(eid[e], ex[e])) mode = kMedium;
       }
-      // rows with more than two entries
+      // rows with more than two entries: the rest from the segment (rare)
 #pragma unroll
-      for (int k = 0; k < kChunk; ++k)
-        for (int p = r0[k] + 2; p < r0[k] + rn[k] && mode == kFast; ++p)
-          if (!mp.add(__ldg(nb.Fid + p), __fmul_rn(lij[k], V::load(nb.Fval + p)))) mode = kMedium;
+      for (int k = 0; k < kChunk; ++k) {
+        if (rn[k] > 2 && mode == kFast) {
+          r0[k] = __ldg(nb.rows + jj[k]).x;
+          for (int p = r0[k] + 2; p < r0[k] + rn[k] && mode == kFast; ++p)
+            if (!mp.add(__ldg(nb.Fid + p), __fmul_rn(lij[k], V::load(nb.Fval + p)))) mode = kMedium;
+        }
+      }
     }
   }
 
   // ---- medium path: a shared-memory map for unions beyond the register map
+  if (mode != kFast) read_own_row();
   if (mode == kMedium) {
     const int slot = atomicAdd(&s_pool, 1);
     mode = kSlow;
@@ -601,21 +638,27 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
     const int off = tile * cap + local_excl;
     out.rows[i] = make_int2(off, kept);
     T* ov = static_cast<T*>(out.vals);
+    // head record: the count and the first two entries written
+    int4 ho = make_int4(kept, 0, 0, 0);
+    auto put = [&](int o, int l, T vt) {
+      out.ids[o] = static_cast<uint16_t>(l);
+      ov[o] = vt;
+      if (o == off) { ho.y = l; ho.z = V::bits(vt); }
+      else if (o == off + 1) { ho.y |= l << 16; ho.w = V::bits(vt); }
+    };
     if (mode == kFast) {
       int o = off;
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
         if (!keep[s]) continue;
-        out.ids[o] = static_cast<uint16_t>(mp.id[s]);
-        ov[o] = V::round(vnew[s]);
+        put(o, mp.id[s], V::round(vnew[s]));
         ++o;
       }
     } else if (mode == kMedium) {
       int o = off;
       for (int s = 0; s < med.cnt; ++s) {
         if (med.f[s] < 0.0f) continue;
-        out.ids[o] = static_cast<uint16_t>(med.id[s]);
-        ov[o] = V::round(med.g[s]);
+        put(o, med.id[s], V::round(med.g[s]));
         ++o;
       }
     } else {
@@ -627,12 +670,12 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
         if (!in_skeleton(F, G)) continue;
         const T vt = V::round(U.value(l == base, F, G, sqrtf(F), S, c) / tot);
         if (V::widen(vt) != 0.0f) {
-          out.ids[o] = static_cast<uint16_t>(l);
-          ov[o] = vt;
+          put(o, l, vt);
           ++o;
         }
       }
     }
+    out.head[i] = ho;
   }
 
   // ---- end of step: the last CTA of the job commits the step ----------------
@@ -721,6 +764,25 @@ __global__ void relayout_kernel(const int2* __restrict__ rows_from, const uint16
 }
 
 template <int DT>
+__global__ void build_head_kernel(const FieldBuf b, int n_v) {
+  using V = Val<DT>;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_v) return;
+  const int2 r = b.rows[i];
+  const typename V::T* vals = static_cast<const typename V::T*>(b.vals);
+  int4 h = make_int4(r.y, 0, 0, 0);
+  if (r.y > 0) {
+    h.y = b.ids[r.x];
+    h.z = V::bits(vals[r.x]);
+  }
+  if (r.y > 1) {
+    h.y |= static_cast<int>(b.ids[r.x + 1]) << 16;
+    h.w = V::bits(vals[r.x + 1]);
+  }
+  b.head[i] = h;
+}
+
+template <int DT>
 __global__ void widen_kernel(const void* __restrict__ src, float* __restrict__ dst, int64_t n) {
   using V = Val<DT>;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -768,6 +830,13 @@ cudaError_t launch_seed(const JobDesc& job, int k, const int32_t* d_seeds, int d
   const int blocks = (job.n_v + 255) / 256;
   LF_DISPATCH(dtype, seed_fill_kernel, blocks, 256, s, job, k);
   seed_scatter_kernel<<<(k + 255) / 256, 256, 0, s>>>(job, k, d_seeds);
+  LF_DISPATCH(dtype, build_head_kernel, blocks, 256, s, job.buf[0], job.n_v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_head(const FieldBuf& b, int n_v, int dtype, cudaStream_t s) {
+  const int blocks = (n_v + 255) / 256;
+  LF_DISPATCH(dtype, build_head_kernel, blocks, 256, s, b, n_v);
   return cudaGetLastError();
 }
 

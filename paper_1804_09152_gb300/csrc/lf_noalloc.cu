@@ -69,11 +69,12 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 extern "C" {
 
 lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers, const int32_t* d_L_rowptr,
-                          const int32_t* d_L_colval, const int32_t* d_rows_in, const uint16_t* d_ids_in,
-                          const float* d_vals_in, int32_t* d_rows_out, uint16_t* d_ids_out, float* d_vals_out,
-                          int32_t tile_cap, const lf_params* params, int64_t* nnz_out, int64_t* need_tile_cap) {
-  if (!d_L_rowptr || !d_L_colval || !d_rows_in || !d_ids_in || !d_vals_in || !d_rows_out || !d_ids_out ||
-      !d_vals_out)
+                          const int32_t* d_L_colval, const int32_t* d_rows_in, const int32_t* d_head_in,
+                          const uint16_t* d_ids_in, const float* d_vals_in, int32_t* d_rows_out,
+                          int32_t* d_head_out, uint16_t* d_ids_out, float* d_vals_out, int32_t tile_cap,
+                          const lf_params* params, int64_t* nnz_out, int64_t* need_tile_cap) {
+  if (!d_L_rowptr || !d_L_colval || !d_rows_in || !d_head_in || !d_ids_in || !d_vals_in || !d_rows_out ||
+      !d_head_out || !d_ids_out || !d_vals_out)
     return noalloc_fail(LF_ERR_INVALID, "null device pointer");
   if (n_v < 1 || n_v > 2147483647 - lf::kTile) return noalloc_fail(LF_ERR_INVALID, "n_v out of range");
   if (n_layers < 2 || n_layers > 65536) return noalloc_fail(LF_ERR_INVALID, "n_layers must be in [2, 65536]");
@@ -84,6 +85,8 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers, cons
     return noalloc_fail(LF_ERR_CAPACITY, "tiles * tile_cap exceeds 2^31 - 1 entries");
   if (!aligned(d_L_colval, 8) || !aligned(d_rows_in, 8) || !aligned(d_rows_out, 8))
     return noalloc_fail(LF_ERR_INVALID, "L_colval and the row arrays must be 8-byte aligned");
+  if (!aligned(d_head_in, 16) || !aligned(d_head_out, 16))
+    return noalloc_fail(LF_ERR_INVALID, "the head arrays must be 16-byte aligned");
   lf_params p;
   lf_default_params(&p);
   if (params) p = *params;
@@ -111,8 +114,10 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers, cons
   job.L_rowptr = d_L_rowptr;
   job.L_colval = reinterpret_cast<const int2*>(d_L_colval);
   job.buf[0] = lf::FieldBuf{const_cast<int2*>(reinterpret_cast<const int2*>(d_rows_in)),
+                            const_cast<int4*>(reinterpret_cast<const int4*>(d_head_in)),
                             const_cast<uint16_t*>(d_ids_in), const_cast<float*>(d_vals_in)};
-  job.buf[1] = lf::FieldBuf{reinterpret_cast<int2*>(d_rows_out), d_ids_out, d_vals_out};
+  job.buf[1] = lf::FieldBuf{reinterpret_cast<int2*>(d_rows_out), reinterpret_cast<int4*>(d_head_out), d_ids_out,
+                            d_vals_out};
   job.st = &d_layout->st;
   job.c = lf::Coefs{static_cast<float>(p.dt),   static_cast<float>(p.mu),   static_cast<float>(p.w_cc),
                     static_cast<float>(p.w_cb), static_cast<float>(p.a_cc), static_cast<float>(p.a_cb),

@@ -28,9 +28,11 @@ def lf():
 
 
 def segment(rp, lay, val, n_v, cap):
-    """Plain CSR -> tile-segmented arrays (rows as (start, count) int32 pairs)."""
+    """Plain CSR -> tile-segmented arrays: rows as (start, count) int32 pairs,
+    head records as (count, id0 | id1 << 16, bits of value 0, bits of value 1)."""
     tiles = (n_v + TILE - 1) // TILE
     rows = np.zeros((n_v, 2), np.int32)
+    head = np.zeros((n_v, 4), np.int32)
     ids = np.zeros(tiles * cap, np.uint16)
     vals = np.zeros(tiles * cap, np.float32)
     for i in range(n_v):
@@ -40,7 +42,14 @@ def segment(rp, lay, val, n_v, cap):
         rows[i] = (start, n)
         ids[start:start + n] = lay[rp[i]:rp[i + 1]]
         vals[start:start + n] = val[rp[i]:rp[i + 1]]
-    return rows, ids, vals
+        head[i, 0] = n
+        if n > 0:
+            head[i, 1] = int(lay[rp[i]])
+            head[i, 2] = np.float32(val[rp[i]]).view(np.int32)
+        if n > 1:
+            head[i, 1] |= int(lay[rp[i] + 1]) << 16
+            head[i, 3] = np.float32(val[rp[i] + 1]).view(np.int32)
+    return rows, head, ids, vals
 
 
 def unsegment(rows, ids, vals):
@@ -75,20 +84,24 @@ def test_noalloc_matches_lf_step_on_two_calls(lf, oracle_mod):
     bufs = []
     for _ in range(2):
         bufs.append((torch.zeros((m.n_v, 2), dtype=torch.int32, device=dev),
+                     torch.zeros((m.n_v, 4), dtype=torch.int32, device=dev),
                      torch.zeros(tiles * cap, dtype=torch.int16, device=dev),
                      torch.zeros(tiles * cap, dtype=torch.float32, device=dev)))
-    rows, ids, vals = segment(*state, m.n_v, cap)
+    rows, head, ids, vals = segment(*state, m.n_v, cap)
     bufs[0][0].copy_(torch.from_numpy(rows))
-    bufs[0][1].copy_(torch.from_numpy(ids.view(np.int16)))
-    bufs[0][2].copy_(torch.from_numpy(vals))
+    bufs[0][1].copy_(torch.from_numpy(head))
+    bufs[0][2].copy_(torch.from_numpy(ids.view(np.int16)))
+    bufs[0][3].copy_(torch.from_numpy(vals))
     stream = torch.cuda.current_stream().cuda_stream
 
     for call in range(2):
         src, dst = bufs[call % 2], bufs[(call + 1) % 2]
         nnz, _ = lf.lf_step_noalloc(stream, m.n_v, 65, d_rp.data_ptr(), d_cv.data_ptr(),
-                                    src[0].data_ptr(), src[1].data_ptr(), src[2].data_ptr(),
-                                    dst[0].data_ptr(), dst[1].data_ptr(), dst[2].data_ptr(), cap)
-        out = unsegment(dst[0].cpu().numpy(), dst[1].cpu().numpy().view(np.uint16), dst[2].cpu().numpy())
+                                    *[x.data_ptr() for x in src], *[x.data_ptr() for x in dst], cap)
+        out = unsegment(dst[0].cpu().numpy(), dst[2].cpu().numpy().view(np.uint16), dst[3].cpu().numpy())
+        # the output's head records describe its rows
+        want_head = segment(*out, m.n_v, cap)[1]
+        assert np.array_equal(dst[1].cpu().numpy(), want_head), f"head records, call {call}"
         ref.step(1)
         want = ref.get_field()
         assert nnz == want[0][-1]
@@ -115,13 +128,12 @@ def test_noalloc_reports_small_segments_and_bad_sizes(lf, oracle_mod):
     lay = ((np.arange(m.n_v) * 7) % (n_layers - 1)).astype(np.int32)
     val = np.ones(m.n_v, np.float32)
     cap = TILE
-    rows, ids, vals = segment(rp, lay, val, m.n_v, cap)
+    rows, head, ids, vals = segment(rp, lay, val, m.n_v, cap)
     dev = torch.device("cuda", 0)
-    d = [torch.from_numpy(x).to(dev) for x in (rp_off, colval.reshape(-1), rows, ids.view(np.int16), vals)]
-    o = [torch.zeros_like(d[2]), torch.zeros_like(d[3]), torch.zeros_like(d[4])]
+    d = [torch.from_numpy(x).to(dev) for x in (rp_off, colval.reshape(-1), rows, head, ids.view(np.int16), vals)]
+    o = [torch.zeros_like(x) for x in d[2:]]
     stream = torch.cuda.current_stream().cuda_stream
-    args = [d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(), d[4].data_ptr(),
-            o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr()]
+    args = [x.data_ptr() for x in d] + [x.data_ptr() for x in o]
     free = lf.lf_default_params(w_cc=0.0, w_cb=0.0)
     with pytest.raises(lf.LFError) as ei:
         lf.lf_step_noalloc(stream, m.n_v, n_layers, *args, cap, free)
