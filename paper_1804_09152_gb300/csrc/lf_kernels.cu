@@ -408,6 +408,22 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
       }
       mp.cnt = own;
     }
+    // The base layer reaches most rows at round-off level; giving it a slot
+    // up front (G = 0, F = 0 until an entry adds to it) spares the insert.
+    // An untouched base slot has F = G = 0, so it is outside the skeleton and
+    // changes nothing.
+    if (mode == kFast && i < n_v && mp.cnt < kSlots) {
+      bool has_base = false;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) has_base = has_base || (s < mp.cnt && mp.id[s] == base);
+      if (!has_base) {
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          if (s == mp.cnt) { mp.id[s] = base; mp.g[s] = 0.0f; mp.f[s] = 0.0f; }
+        }
+        ++mp.cnt;
+      }
+    }
     // ---- G = sum_j L_ij F(j, .): neighbours in batches of kChunk; the first
     // two entries of every row in the batch are loaded before any is used
     for (int qb = nb.q0; qb < nb.q1; qb += kChunk) {
@@ -466,14 +482,22 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
           hit[e] = hit[e] || m;
         }
       }
-      // layers new to the map, in entry order (rare)
-      bool all_hit = true;
+      // layers new to the map, in entry order: only the missed entries are
+      // visited (each fetched from the batch arrays by a select chain)
+      unsigned miss = 0u;
 #pragma unroll
-      for (int e = 0; e < kE; ++e) all_hit = all_hit && hit[e];
-      if (!all_hit) {
+      for (int e = 0; e < kE; ++e) miss |= hit[e] ? 0u : (1u << e);
+      while (miss != 0u && mode == kFast) {
+        const int e = __ffs(miss) - 1;
+        miss &= miss - 1u;
+        int le = -2;
+        float xe = 0.0f;
 #pragma unroll
-        for (int e = 0; e < kE; ++e)
-          if (!hit[e] && mode == kFast && !mp.add(eid[e], ex[e])) mode = kMedium;
+        for (int q = 0; q < kE; ++q) {
+          le = (q == e) ? eid[q] : le;
+          xe = (q == e) ? ex[q] : xe;
+        }
+        if (!mp.add(le, xe)) mode = kMedium;
       }
       // rows with more than two entries: the rest from the segment (rare)
 #pragma unroll
