@@ -384,6 +384,11 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
   med.id = nullptr;
   med.g = med.f = nullptr;
 
+  // The base layer is kept apart from the cell slots: its G and F live in
+  // gB / fB and it joins the slots (as the largest id) after the gather.  Most
+  // rows hold it at round-off level, as their second entry.
+  float gB = 0.0f, fB = 0.0f;
+  int own_cells = own;              // own entries other than the base layer
   if (i < n_v) {
     if (own > kSlots) {
       mode = kMedium;
@@ -396,7 +401,6 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
         mp.id[1] = (h_own.y >> 16) & 0xffff;
         mp.f[1] = V::from_bits(h_own.w);
       }
-      mp.cnt = own;
     } else {
       read_own_row();
 #pragma unroll
@@ -406,28 +410,30 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
           mp.f[s] = V::load(nb.Fval + nb.p0 + s);
         }
       }
-      mp.cnt = own;
     }
-    // The base layer reaches most rows at round-off level; giving it a slot
-    // up front (G = 0, F = 0 until an entry adds to it) spares the insert.
-    // An untouched base slot has F = G = 0, so it is outside the skeleton and
-    // changes nothing.
-    if (mode == kFast && i < n_v && mp.cnt < kSlots) {
-      bool has_base = false;
+    if (mode == kFast && own > 0) {
+      // ids ascend within a row and the base layer is the largest id, so an
+      // own base entry is the last one
+      int last = -1;
+      float flast = 0.0f;
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) has_base = has_base || (s < mp.cnt && mp.id[s] == base);
-      if (!has_base) {
+      for (int s = 0; s < kSlots; ++s) {
+        last = (s == own - 1) ? mp.id[s] : last;
+        flast = (s == own - 1) ? mp.f[s] : flast;
+      }
+      if (last == base) {
+        fB = flast;
+        own_cells = own - 1;
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) {
-          if (s == mp.cnt) { mp.id[s] = base; mp.g[s] = 0.0f; mp.f[s] = 0.0f; }
-        }
-        ++mp.cnt;
+        for (int s = 0; s < kSlots; ++s)
+          if (s == own - 1) { mp.id[s] = -1; mp.f[s] = 0.0f; }
       }
     }
-    // ---- G = sum_j L_ij F(j, .): neighbours in batches of kChunk; the first
-    // two entries of every row in the batch are loaded before any is used
+    mp.cnt = own_cells;
+    // ---- G = sum_j L_ij F(j, .): neighbours in batches of kChunk; the head
+    // records of the batch's rows are loaded before any is used
     for (int qb = nb.q0; qb < nb.q1; qb += kChunk) {
-      int jj[kChunk], r0[kChunk], rn[kChunk];
+      int jj[kChunk], rn[kChunk];
       float lij[kChunk];
 #pragma unroll
       for (int k = 0; k < kChunk; ++k) {
@@ -439,7 +445,6 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
           lij[k] = __int_as_float(cv.y);
         }
       }
-      // head records of the batch's rows: count and first two entries
       int4 hj[kChunk];
 #pragma unroll
       for (int k = 0; k < kChunk; ++k) {
@@ -452,61 +457,92 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
       }
       if (mode != kFast) continue;
       // the first two entries of each row of the batch; -2 marks "no entry"
-      constexpr int kE = 2 * kChunk;
-      int eid[kE];
-      float ex[kE];
+      int e0[kChunk], e1[kChunk];
+      float x0[kChunk], x1[kChunk];
+      bool simple = true;           // every row: at most a cell, then the base layer
 #pragma unroll
       for (int k = 0; k < kChunk; ++k) {
-        eid[2 * k] = eid[2 * k + 1] = -2;
-        ex[2 * k] = ex[2 * k + 1] = 0.0f;
+        e0[k] = e1[k] = -2;
+        x0[k] = x1[k] = 0.0f;
         if (rn[k] > 0) {
-          eid[2 * k] = hj[k].y & 0xffff;
-          ex[2 * k] = __fmul_rn(lij[k], V::from_bits(hj[k].z));
+          e0[k] = hj[k].y & 0xffff;
+          x0[k] = __fmul_rn(lij[k], V::from_bits(hj[k].z));
         }
         if (rn[k] > 1) {
-          eid[2 * k + 1] = (hj[k].y >> 16) & 0xffff;
-          ex[2 * k + 1] = __fmul_rn(lij[k], V::from_bits(hj[k].w));
+          e1[k] = (hj[k].y >> 16) & 0xffff;
+          x1[k] = __fmul_rn(lij[k], V::from_bits(hj[k].w));
+        }
+        simple = simple && rn[k] <= 2 && (rn[k] < 2 || e1[k] == base);
+      }
+      if (simple) {
+        // base contributions, one per row at most, in row order
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+          gB = (e0[k] == base) ? __fadd_rn(gB, x0[k]) : gB;
+          gB = (e1[k] == base) ? __fadd_rn(gB, x1[k]) : gB;
+          if (e0[k] == base) e0[k] = -2;
+        }
+        // cell entries (first entries only): slot x entry compare matrix, each
+        // slot summing its entries in row order (empty slots hold -1)
+        bool hit[kChunk];
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) hit[k] = e0[k] < 0;
+#pragma unroll
+        for (int s2 = 0; s2 < kSlots; ++s2) {
+#pragma unroll
+          for (int k = 0; k < kChunk; ++k) {
+            const bool m = e0[k] == mp.id[s2];
+            mp.g[s2] = m ? __fadd_rn(mp.g[s2], x0[k]) : mp.g[s2];
+            hit[k] = hit[k] || m;
+          }
+        }
+        // cells new to the map, in row order (a layer is new in all of its
+        // entries of the batch or in none)
+        unsigned miss = 0u;
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) miss |= hit[k] ? 0u : (1u << k);
+        while (miss != 0u && mode == kFast) {
+          const int k = __ffs(miss) - 1;
+          miss &= miss - 1u;
+          int le = -2;
+          float xe = 0.0f;
+#pragma unroll
+          for (int q = 0; q < kChunk; ++q) {
+            le = (q == k) ? e0[q] : le;
+            xe = (q == k) ? x0[q] : xe;
+          }
+          if (!mp.add(le, xe)) mode = kMedium;
+        }
+      } else {
+        // rows with two cells or more than two entries (transients, band
+        // vertices): every entry in row order, strictly sequential
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+          if (rn[k] <= 0 || mode != kFast) continue;
+          const int start = rn[k] > 2 ? __ldg(nb.rows + jj[k]).x : 0;
+          for (int p = 0; p < rn[k] && mode == kFast; ++p) {
+            int l;
+            float x;
+            if (p == 0) { l = e0[k]; x = x0[k]; }
+            else if (p == 1) { l = e1[k]; x = x1[k]; }
+            else { l = __ldg(nb.Fid + start + p); x = __fmul_rn(lij[k], V::load(nb.Fval + start + p)); }
+            if (l == base) gB = __fadd_rn(gB, x);
+            else if (!mp.add(l, x)) mode = kMedium;
+          }
         }
       }
-      // entries whose layer already has a slot: slot x entry compare matrix,
-      // each slot summing its entries in entry order (empty slots hold -1)
-      bool hit[kE];
+    }
+    // the base layer joins the slots last (largest id); with six cells
+    // already there the vertex takes the next tier
+    if (mode == kFast) {
+      if (mp.cnt >= kSlots) {
+        mode = kMedium;
+      } else {
 #pragma unroll
-      for (int e = 0; e < kE; ++e) hit[e] = eid[e] < 0;
-#pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
-#pragma unroll
-        for (int e = 0; e < kE; ++e) {
-          const bool m = eid[e] == mp.id[s];
-          mp.g[s] = m ? __fadd_rn(mp.g[s], ex[e]) : mp.g[s];
-          hit[e] = hit[e] || m;
+        for (int s2 = 0; s2 < kSlots; ++s2) {
+          if (s2 == mp.cnt) { mp.id[s2] = base; mp.g[s2] = gB; mp.f[s2] = fB; }
         }
-      }
-      // layers new to the map, in entry order: only the missed entries are
-      // visited (each fetched from the batch arrays by a select chain)
-      unsigned miss = 0u;
-#pragma unroll
-      for (int e = 0; e < kE; ++e) miss |= hit[e] ? 0u : (1u << e);
-      while (miss != 0u && mode == kFast) {
-        const int e = __ffs(miss) - 1;
-        miss &= miss - 1u;
-        int le = -2;
-        float xe = 0.0f;
-#pragma unroll
-        for (int q = 0; q < kE; ++q) {
-          le = (q == e) ? eid[q] : le;
-          xe = (q == e) ? ex[q] : xe;
-        }
-        if (!mp.add(le, xe)) mode = kMedium;
-      }
-      // rows with more than two entries: the rest from the segment (rare)
-#pragma unroll
-      for (int k = 0; k < kChunk; ++k) {
-        if (rn[k] > 2 && mode == kFast) {
-          r0[k] = __ldg(nb.rows + jj[k]).x;
-          for (int p = r0[k] + 2; p < r0[k] + rn[k] && mode == kFast; ++p)
-            if (!mp.add(__ldg(nb.Fid + p), __fmul_rn(lij[k], V::load(nb.Fval + p)))) mode = kMedium;
-        }
+        ++mp.cnt;
       }
     }
   }
@@ -554,9 +590,10 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
   if (i < n_v) {
     if (mode == kFast) {
       // ---- fast path: diagonal, skeleton, update over the register map ------
+      // diagonal: the own entries (the own cells, then the base layer)
 #pragma unroll
       for (int s = 0; s < kSlots; ++s)
-        if (s < own) mp.g[s] = fmaf(-nb.dsum, mp.f[s], mp.g[s]);
+        if (s < own_cells || (s == mp.cnt - 1 && own_cells < own)) mp.g[s] = fmaf(-nb.dsum, mp.f[s], mp.g[s]);
       // slots in ascending layer order (empty slots, id -1, last): the sums
       // below then run in the same order as on the other paths, and the row
       // is written in slot order
