@@ -82,7 +82,7 @@ __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol
 
 constexpr int kBlock = kTile;   // threads (= vertices) per CTA
 #ifndef LF_SLOTS
-#define LF_SLOTS 6
+#define LF_SLOTS 5
 #endif
 constexpr int kSlots = LF_SLOTS; // register map slots of the fast path
 constexpr int kChunk = 4;       // neighbours fetched per batch
@@ -226,7 +226,7 @@ struct SlotMap {
       if (s < cnt && !found && id[s] == l) { g[s] = __fadd_rn(g[s], x); found = true; }
     }
     if (found) return true;
-    if (cnt >= kSlots) return false;
+    if (cnt >= kSlots - 1) return false;    // one slot stays for the base layer
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
       if (s == cnt) { id[s] = l; g[s] = x; }
@@ -248,10 +248,12 @@ struct SlotMap {
     if constexpr (kSlots == 4) {
       cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
     } else {
+      // the base layer (largest id) is the last live slot, so sorting the
+      // first kSlots - 1 slots orders them all
 #pragma unroll
-      for (int r = 0; r < kSlots; ++r)
+      for (int r = 0; r < kSlots - 1; ++r)
 #pragma unroll
-        for (int a = r & 1; a + 1 < kSlots; a += 2) cswap(a, a + 1);
+        for (int a = r & 1; a + 1 < kSlots - 1; a += 2) cswap(a, a + 1);
     }
   }
 };
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
 #pragma unroll
         for (int k = 0; k < kChunk; ++k) hit[k] = e0[k] < 0;
 #pragma unroll
-        for (int s2 = 0; s2 < kSlots; ++s2) {
+        for (int s2 = 0; s2 < kSlots - 1; ++s2) {   // cells: the base slot comes last
 #pragma unroll
           for (int k = 0; k < kChunk; ++k) {
             const bool m = e0[k] == mp.id[s2];
@@ -616,10 +618,11 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
         }
       }
       if (!(tot > 0.0f)) zero_sum = true;
+      const float rtot = 1.0f / tot;           // normalisation: one division per vertex
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
         if (ins[s]) {
-          const float vs = V::widen(V::round(vnew[s] / tot));
+          const float vs = V::widen(V::round(__fmul_rn(vnew[s], rtot)));
           if (vs != 0.0f) { keep[s] = true; vnew[s] = vs; ++kept; }
         }
       }
@@ -637,9 +640,10 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
         }
       }
       if (!(tot > 0.0f)) zero_sum = true;
+      const float rtot = 1.0f / tot;
       for (int s = 0; s < med.cnt; ++s) {
         if (med.f[s] < 0.0f) continue;
-        const float vs = V::widen(V::round(med.g[s] / tot));
+        const float vs = V::widen(V::round(__fmul_rn(med.g[s], rtot)));
         if (vs != 0.0f) { med.g[s] = vs; ++kept; }
         else med.f[s] = -1.0f;
       }
@@ -658,7 +662,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
       if (!(tot > 0.0f)) zero_sum = true;
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
-        if (in_skeleton(F, G) && V::widen(V::round(U.value(l == base, F, G, sqrtf(F), S, c) / tot)) != 0.0f)
+        if (in_skeleton(F, G) && V::widen(V::round(__fmul_rn(U.value(l == base, F, G, sqrtf(F), S, c), 1.0f / tot))) != 0.0f)
           ++kept;
       }
     }
@@ -729,7 +733,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
         if (!in_skeleton(F, G)) continue;
-        const T vt = V::round(U.value(l == base, F, G, sqrtf(F), S, c) / tot);
+        const T vt = V::round(__fmul_rn(U.value(l == base, F, G, sqrtf(F), S, c), 1.0f / tot));
         if (V::widen(vt) != 0.0f) {
           put(o, l, vt);
           ++o;

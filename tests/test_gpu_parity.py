@@ -197,7 +197,7 @@ def test_large_layer_unions_match(lf, oracle_mod, per_row, n_layers):
     mesh.set_field(rp, ids, vals, n_layers)
     mesh.step(1)
     st = mesh.stats()
-    assert st["map_slots"] == 6
+    assert st["map_slots"] == 5
     L = oracle_mod.cotan_laplacian(m.V, m.F)
     Fin = oracle_mod.Field(rp, ids, vals.astype(np.float64), n_layers)
     Fo, _, mg = oracle_mod.step(L, Fin, margins=True)
