@@ -85,7 +85,7 @@ constexpr int kBlock = kTile;   // threads (= vertices) per CTA
 #define LF_SLOTS 5
 #endif
 constexpr int kSlots = LF_SLOTS; // register map slots of the fast path
-constexpr int kChunk = 4;       // neighbours fetched per batch
+constexpr int kChunk = 2;       // neighbours fetched per batch
 constexpr int kPool = 4;        // medium-path maps per CTA
 constexpr int kMed = 32;        // slots of a medium-path map
 
