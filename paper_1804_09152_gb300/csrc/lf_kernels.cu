@@ -100,41 +100,60 @@ struct VertexSums {
 // Algorithm 1's double sum is -(mu/n)[1/2 (n A_j - sum A) + (n W_j - sum W)]
 // and its band term (mu/n) sqrt(F_j) sum_k e_jk sqrt(F_k).
 struct Update {
-  float fn, fnc, sumA, sumW, mun, sqFb;
+  // d_j is linear in G_j and F_j once the per-vertex sums are known:
+  //   cell: d = (mu/n) (-K + gA G_j + fW F_j + sqrt(F_j) (R0 - e_cc sqrt(F_j)))
+  //   base: d = (mu/n) (-Kb + sqrt(F_b) Rb)
+  // with K = 1/2 (n a_cc sum_G + n [b] a_cb G_b - sum A) + (n w_cc sum_F + n [b] w_cb F_b - sum W),
+  // gA = n a_cc / 2, fW = n w_cc, R0 = e_cc sum_sqrtF + [b] e_cb sqrt(F_b),
+  // Kb = 1/2 (n a_cb sum_G - sum A) + (n w_cb sum_F - sum W), Rb = e_bc sum_sqrtF.
+  // All roundings are explicit (no contraction left to the compiler), so every
+  // tier that inlines this gives bit-identical results.
+  float mun, K, gA, fW, R0, eS, Kb, Rb;
   __device__ __forceinline__ Update(const VertexSums& s, const Coefs& c) {
     const int n = s.nC + s.hasb;
-    fn = static_cast<float>(n);
-    fnc = static_cast<float>(s.nC);
-    // explicit roundings throughout (no contraction left to the compiler), so
-    // that every code path that inlines this gives bit-identical results
+    const float fn = static_cast<float>(n);
+    const float fnc = static_cast<float>(s.nC);
     const float bA = s.hasb ? __fmul_rn(c.a_cb, __fmaf_rn(fnc, s.Gb, s.sG)) : 0.0f;
     const float bW = s.hasb ? __fmul_rn(c.w_cb, __fmaf_rn(fnc, s.Fb, s.sF)) : 0.0f;
-    sumA = __fmaf_rn(__fmul_rn(c.a_cc, __fsub_rn(fnc, 1.0f)), s.sG, bA);
-    sumW = __fmaf_rn(__fmul_rn(c.w_cc, __fsub_rn(fnc, 1.0f)), s.sF, bW);
+    const float sumA = __fmaf_rn(__fmul_rn(c.a_cc, __fsub_rn(fnc, 1.0f)), s.sG, bA);
+    const float sumW = __fmaf_rn(__fmul_rn(c.w_cc, __fsub_rn(fnc, 1.0f)), s.sF, bW);
+    const float A0 = __fmaf_rn(c.a_cc, s.sG, s.hasb ? __fmul_rn(c.a_cb, s.Gb) : 0.0f);
+    const float W0 = __fmaf_rn(c.w_cc, s.sF, s.hasb ? __fmul_rn(c.w_cb, s.Fb) : 0.0f);
+    K = __fmaf_rn(0.5f, __fmaf_rn(fn, A0, -sumA), __fmaf_rn(fn, W0, -sumW));
+    gA = __fmul_rn(0.5f, __fmul_rn(fn, c.a_cc));
+    fW = __fmul_rn(fn, c.w_cc);
+    R0 = __fmaf_rn(c.e_cc, s.r, s.hasb ? __fmul_rn(c.e_cb, s.sqFb) : 0.0f);
+    eS = c.e_cc;
+    Kb = __fmaf_rn(0.5f, __fmaf_rn(fn, __fmul_rn(c.a_cb, s.sG), -sumA),
+                   __fmaf_rn(fn, __fmul_rn(c.w_cb, s.sF), -sumW));
+    Rb = __fmul_rn(c.e_bc, s.r);
     mun = c.mu / fn;
-    sqFb = s.sqFb;
   }
-  // f, g: F and G of the entry; sqf = sqrt(f), computed once by the caller.
-  __device__ __forceinline__ float value(bool is_base, float f, float g, float sqf, const VertexSums& s,
+  // f, g: F and G of the entry; sqf = root(f), computed once by the caller.
+  __device__ __forceinline__ float value(bool is_base, float f, float g, float sqf, const VertexSums&,
                                          const Coefs& c) const {
-    float A, W, R;
-    if (is_base) {
-      A = __fmul_rn(c.a_cb, s.sG);
-      W = __fmul_rn(c.w_cb, s.sF);
-      R = __fmul_rn(c.e_bc, s.r);
-    } else {
-      A = __fmaf_rn(c.a_cc, __fsub_rn(s.sG, g), s.hasb ? __fmul_rn(c.a_cb, s.Gb) : 0.0f);
-      W = __fmaf_rn(c.w_cc, __fsub_rn(s.sF, f), s.hasb ? __fmul_rn(c.w_cb, s.Fb) : 0.0f);
-      R = __fmaf_rn(c.e_cc, __fsub_rn(s.r, sqf), s.hasb ? __fmul_rn(c.e_cb, sqFb) : 0.0f);
-    }
-    const float inner = __fmaf_rn(0.5f, __fmaf_rn(fn, A, -sumA), __fmaf_rn(fn, W, -sumW));
-    const float d = __fmaf_rn(-mun, inner, __fmul_rn(__fmul_rn(mun, sqf), R));
-    float v = __fmaf_rn(d, c.dt, f);
+    const float k = is_base ? Kb : K;
+    const float ga = is_base ? 0.0f : gA;
+    const float fw = is_base ? 0.0f : fW;
+    const float r0 = is_base ? Rb : R0;
+    const float es = is_base ? 0.0f : eS;
+    float t = __fmaf_rn(ga, g, -k);
+    t = __fmaf_rn(fw, f, t);
+    t = __fmaf_rn(sqf, __fmaf_rn(-es, sqf, r0), t);
+    float v = __fmaf_rn(__fmul_rn(mun, t), c.dt, f);
     if (v > 1.0f) v = 1.0f;
     if (v <= 0.0f) v = 0.0f;
     return v;
   }
 };
+
+// Square root of a field value for the band term: the hardware's approximate
+// root (sqrt.approx.f32, a few ulp), the same instruction in every tier.
+__device__ __forceinline__ float root(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 __device__ __forceinline__ bool in_skeleton(float f, float g) { return f > 0.0f || (f == 0.0f && g > 0.0f); }
 
@@ -297,7 +316,7 @@ __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* s_red) {
 enum : int { kFast = 0, kMedium = 1, kSlow = 2 };
 
 template <int DT>
-__global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_constant__ BatchParams P) {
+__global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_constant__ BatchParams P) {
   using V = Val<DT>;
   using T = typename V::T;
   constexpr int kWarps = kBlock / 32;
@@ -602,7 +621,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
       mp.sort();
       float sq[kSlots];
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) sq[s] = sqrtf(mp.f[s]);
+      for (int s = 0; s < kSlots; ++s) sq[s] = root(mp.f[s]);
       bool ins[kSlots];
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
@@ -629,11 +648,11 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
     } else if (mode == kMedium) {
       // ---- medium path: the same update over the shared-memory map ----------
       for (int s = 0; s < med.cnt; ++s)
-        if (in_skeleton(med.f[s], med.g[s])) add_to_sums(S, med.id[s] == base, med.f[s], med.g[s], sqrtf(med.f[s]));
+        if (in_skeleton(med.f[s], med.g[s])) add_to_sums(S, med.id[s] == base, med.f[s], med.g[s], root(med.f[s]));
       const Update U(S, c);
       for (int s = 0; s < med.cnt; ++s) {
         if (in_skeleton(med.f[s], med.g[s])) {
-          med.g[s] = U.value(med.id[s] == base, med.f[s], med.g[s], sqrtf(med.f[s]), S, c);
+          med.g[s] = U.value(med.id[s] == base, med.f[s], med.g[s], root(med.f[s]), S, c);
           tot += med.g[s];
         } else {
           med.f[s] = -1.0f;                      // not in the skeleton
@@ -652,17 +671,17 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
       float G, F;
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
-        if (in_skeleton(F, G)) add_to_sums(S, l == base, F, G, sqrtf(F));
+        if (in_skeleton(F, G)) add_to_sums(S, l == base, F, G, root(F));
       }
       const Update U(S, c);
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
-        if (in_skeleton(F, G)) tot += U.value(l == base, F, G, sqrtf(F), S, c);
+        if (in_skeleton(F, G)) tot += U.value(l == base, F, G, root(F), S, c);
       }
       if (!(tot > 0.0f)) zero_sum = true;
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
-        if (in_skeleton(F, G) && V::widen(V::round(__fmul_rn(U.value(l == base, F, G, sqrtf(F), S, c), 1.0f / tot))) != 0.0f)
+        if (in_skeleton(F, G) && V::widen(V::round(__fmul_rn(U.value(l == base, F, G, root(F), S, c), 1.0f / tot))) != 0.0f)
           ++kept;
       }
     }
@@ -733,7 +752,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel_impl(const __grid_const
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
         if (!in_skeleton(F, G)) continue;
-        const T vt = V::round(__fmul_rn(U.value(l == base, F, G, sqrtf(F), S, c), 1.0f / tot));
+        const T vt = V::round(__fmul_rn(U.value(l == base, F, G, root(F), S, c), 1.0f / tot));
         if (V::widen(vt) != 0.0f) {
           put(o, l, vt);
           ++o;
