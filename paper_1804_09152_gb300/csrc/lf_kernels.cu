@@ -261,14 +261,14 @@ struct SlotMap {
     g[a] = sw ? gb : ga;  g[b] = sw ? ga : gb;
     f[a] = sw ? fb : fa;  f[b] = sw ? fa : fb;
   }
-  // Sorting network on the slots (ids are distinct): the optimal five
-  // exchanges for four slots, odd-even transposition otherwise.
+  // Sorting network on the cell slots (ids are distinct; empty slots hold -1,
+  // which sorts last).  The base layer, the largest id, is the last live
+  // slot, so ordering the first kSlots - 1 slots orders them all: the optimal
+  // five exchanges for four, odd-even transposition otherwise.
   __device__ __forceinline__ void sort() {
-    if constexpr (kSlots == 4) {
+    if constexpr (kSlots - 1 == 4) {
       cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
     } else {
-      // the base layer (largest id) is the last live slot, so sorting the
-      // first kSlots - 1 slots orders them all
 #pragma unroll
       for (int r = 0; r < kSlots - 1; ++r)
 #pragma unroll
@@ -296,19 +296,6 @@ struct MedMap {
   }
 };
 
-// Block-wide sum of one value per thread (all threads get the result).
-__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* s_red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) s_red[warp] = v;
-  __syncthreads();
-  unsigned s = 0;
-#pragma unroll
-  for (int w = 0; w < kBlock / 32; ++w) s += s_red[w];
-  __syncthreads();
-  return s;
-}
 
 // ---------------------------------------------------------------------------
 // the step kernel
@@ -696,16 +683,24 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
     const int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) s_warp_cnt[warp] = x;
+  // the skeleton sizes are reduced per warp alongside, so one barrier serves both
+  unsigned sk = static_cast<unsigned>(nsk);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sk += __shfl_xor_sync(0xffffffffu, sk, o);
+  if (lane == 31) {
+    s_warp_cnt[warp] = x;
+    s_red[warp] = sk;
+  }
   const bool bad_sum = __syncthreads_or(zero_sum);
   int warp_off = 0, tile_total = 0;
+  unsigned tile_sk = 0;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) {
     if (w < warp) warp_off += s_warp_cnt[w];
     tile_total += s_warp_cnt[w];
+    tile_sk += s_red[w];
   }
   const int local_excl = warp_off + x - kept;
-  const unsigned tile_sk = block_sum(static_cast<unsigned>(nsk), s_red);
 
   bool write = !bad_sum;
   if (t == 0 && bad_sum) atomicOr(&st->err, ERR_ZERO_SUM);
