@@ -283,7 +283,7 @@ def run_ours(args, wl):
         "roofline": roofline,
         "e2e": {"value": e2e_units / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "jobs": n_e2e},
-        "gpu_launches": args.steps * (T + 3) + retries,
+        "gpu_launches": args.steps * (T + 4) + retries,   # seed (fill, scatter, head records), steps, labels
         "clocks": clk.summary(),
         "wall_s": wall,
     }
