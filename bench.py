@@ -46,7 +46,7 @@ WORKLOADS = {
 
 # DRAM bytes of one step-kernel launch from an ncu capture of the grid512
 # workload, valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"kernel_sha": "49c71d211447f799", "bytes_per_launch": 17863083}
+NCU_TRAFFIC = {"kernel_sha": "0ea4d3d1fff8227e", "bytes_per_launch": 17856597}
 L2_FLUSH_BYTES = 512 << 20
 
 
