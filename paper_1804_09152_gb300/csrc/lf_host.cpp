@@ -14,6 +14,8 @@
 #include <string>
 #include <utility>
 #include <vector>
+#include <atomic>
+#include <thread>
 
 #include "../../include/lf.h"
 #include "lf_internal.h"
@@ -158,57 +160,110 @@ bool params_ok(const lf_params& p, std::string& why) {
   return true;
 }
 
+// Runs fn(lo, hi) over [0, n) split among up to 16 host threads (one thread
+// below `grain` items).
+template <class Fn>
+void parallel_for(int64_t n, int64_t grain, Fn fn) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int64_t nt = std::min<int64_t>({static_cast<int64_t>(std::min(hw, 16u)), (n + grain - 1) / grain});
+  if (nt <= 1) {
+    fn(int64_t{0}, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(static_cast<size_t>(nt));
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back(fn, n * t / nt, n * (t + 1) / nt);
+  for (auto& x : th) x.join();
+}
+
 // Cotangent weights: for the corner p of triangle (p, q, s), the edge (q, s)
-// receives cot(angle at p) / 2.  Returns false on a zero-area face.
+// receives cot(angle at p) / 2.  Returns false on a zero-area face.  The
+// per-face and per-vertex passes run on host threads; every sum is taken in
+// face order, so the result does not depend on the thread count.
 bool cotan_rows(int64_t n_v, const double* V, int64_t n_f, const int32_t* F,
                 std::vector<int64_t>& rp, std::vector<int32_t>& col, std::vector<double>& val,
                 std::string& why) {
+  // half cotangent of each corner
+  std::vector<double> hc(3 * static_cast<size_t>(n_f));
+  std::atomic<int64_t> first_bad{n_f};
+  parallel_for(n_f, 1 << 15, [&](int64_t lo, int64_t hi) {
+    for (int64_t f = lo; f < hi; ++f) {
+      const int32_t v[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+      for (int c = 0; c < 3; ++c) {
+        const double* P = V + 3 * static_cast<int64_t>(v[c]);
+        const double* Q = V + 3 * static_cast<int64_t>(v[(c + 1) % 3]);
+        const double* S = V + 3 * static_cast<int64_t>(v[(c + 2) % 3]);
+        const double ux = Q[0] - P[0], uy = Q[1] - P[1], uz = Q[2] - P[2];
+        const double wx = S[0] - P[0], wy = S[1] - P[1], wz = S[2] - P[2];
+        const double cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+        const double twice_area = std::sqrt(cx * cx + cy * cy + cz * cz);
+        if (!(twice_area > 0.0) || !std::isfinite(twice_area)) {
+          int64_t cur = first_bad.load();
+          while (f < cur && !first_bad.compare_exchange_weak(cur, f)) {
+          }
+          hc[3 * static_cast<size_t>(f) + c] = 0.0;
+          continue;
+        }
+        hc[3 * static_cast<size_t>(f) + c] = 0.5 * (ux * wx + uy * wy + uz * wz) / twice_area;
+      }
+    }
+  });
+  if (first_bad.load() < n_f) {
+    why = "face " + std::to_string(first_bad.load()) + " has zero area";
+    return false;
+  }
+  // contributions per vertex, in face order: corner p of face f adds its
+  // half cotangent to the edge between the other two corners, at both ends
   std::vector<int64_t> start(static_cast<size_t>(n_v) + 1, 0);
   for (int64_t f = 0; f < n_f; ++f)
     for (int c = 0; c < 3; ++c) start[static_cast<size_t>(F[3 * f + c]) + 1] += 2;
   for (int64_t i = 0; i < n_v; ++i) start[i + 1] += start[i];
   std::vector<std::pair<int32_t, double>> ent(static_cast<size_t>(start[n_v]));
-  std::vector<int64_t> fill(start.begin(), start.end() - 1);
-  for (int64_t f = 0; f < n_f; ++f) {
-    const int32_t v[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
-    for (int c = 0; c < 3; ++c) {
-      const int32_t p = v[c], q = v[(c + 1) % 3], s = v[(c + 2) % 3];
-      const double* P = V + 3 * static_cast<int64_t>(p);
-      const double* Q = V + 3 * static_cast<int64_t>(q);
-      const double* S = V + 3 * static_cast<int64_t>(s);
-      const double ux = Q[0] - P[0], uy = Q[1] - P[1], uz = Q[2] - P[2];
-      const double wx = S[0] - P[0], wy = S[1] - P[1], wz = S[2] - P[2];
-      const double cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
-      const double twice_area = std::sqrt(cx * cx + cy * cy + cz * cz);
-      if (!(twice_area > 0.0) || !std::isfinite(twice_area)) {
-        why = "face " + std::to_string(f) + " has zero area";
-        return false;
+  {
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t f = 0; f < n_f; ++f) {
+      const int32_t v[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+      for (int c = 0; c < 3; ++c) {
+        const int32_t q = v[(c + 1) % 3], t = v[(c + 2) % 3];
+        const double h = hc[3 * static_cast<size_t>(f) + c];
+        ent[static_cast<size_t>(fill[q]++)] = {t, h};
+        ent[static_cast<size_t>(fill[t]++)] = {q, h};
       }
-      const double half_cot = 0.5 * (ux * wx + uy * wy + uz * wz) / twice_area;
-      ent[static_cast<size_t>(fill[q]++)] = {s, half_cot};
-      ent[static_cast<size_t>(fill[s]++)] = {q, half_cot};
     }
   }
+  // per vertex: sort by column (stable: equal columns keep face order), sum
+  // duplicates; then the offsets and the copy
+  std::vector<int64_t> uniq(static_cast<size_t>(n_v), 0);
+  parallel_for(n_v, 1 << 14, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      auto b = ent.begin() + start[i], e = ent.begin() + start[i + 1];
+      std::stable_sort(b, e, [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+        return x.first < y.first;
+      });
+      int64_t n = 0;
+      for (auto it = b; it != e;) {
+        auto jt = it;
+        double w = 0.0;
+        while (jt != e && jt->first == it->first) { w += jt->second; ++jt; }
+        *(b + n) = {it->first, w};       // compacted in place: n never passes it
+        ++n;
+        it = jt;
+      }
+      uniq[static_cast<size_t>(i)] = n;
+    }
+  });
   rp.assign(static_cast<size_t>(n_v) + 1, 0);
-  col.clear();
-  val.clear();
-  col.reserve(ent.size() / 2 + 16);
-  val.reserve(ent.size() / 2 + 16);
-  for (int64_t i = 0; i < n_v; ++i) {
-    auto b = ent.begin() + start[i], e = ent.begin() + start[i + 1];
-    std::stable_sort(b, e, [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
-      return x.first < y.first;
-    });
-    for (auto it = b; it != e;) {
-      auto jt = it;
-      double w = 0.0;
-      while (jt != e && jt->first == it->first) { w += jt->second; ++jt; }
-      col.push_back(it->first);
-      val.push_back(w);
-      it = jt;
-    }
-    rp[static_cast<size_t>(i) + 1] = static_cast<int64_t>(col.size());
-  }
+  for (int64_t i = 0; i < n_v; ++i) rp[static_cast<size_t>(i) + 1] = rp[static_cast<size_t>(i)] + uniq[static_cast<size_t>(i)];
+  col.resize(static_cast<size_t>(rp[static_cast<size_t>(n_v)]));
+  val.resize(col.size());
+  parallel_for(n_v, 1 << 14, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      for (int64_t k = 0; k < uniq[static_cast<size_t>(i)]; ++k) {
+        const auto& x = ent[static_cast<size_t>(start[i] + k)];
+        col[static_cast<size_t>(rp[static_cast<size_t>(i)] + k)] = x.first;
+        val[static_cast<size_t>(rp[static_cast<size_t>(i)] + k)] = x.second;
+      }
+  });
   return true;
 }
 
