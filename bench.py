@@ -498,7 +498,8 @@ def run_serve(args):
                 while time.monotonic_ns() < due:
                     time.sleep(min(1e-3, max(0.0, (due - time.monotonic_ns()) / 1e9)))
                 m = cache[(sp.kind, sp.size)]
-                ids.append((srv.submit(m.V, m.F, sd, sp.steps, arrival_ns=due), m.n_v))
+                ids.append((srv.submit(m.V, m.F, sd, sp.steps, arrival_ns=due, lloyd_rounds=sp.lloyd_rounds,
+                                       extract_dual=sp.dual), m.n_v))
             assert srv.drain(3600.0) == lf.LF_OK
             t_end = time.monotonic_ns()
             lat, units = [], 0
@@ -517,8 +518,13 @@ def run_serve(args):
         with lf.Mesh(m.V, m.F) as mesh:
             mesh.seed(sd)
             mesh.step(sp.steps)
-            mesh.labels()
             units_plain += mesh.stats()["skeleton_total"]
+            for _ in range(sp.lloyd_rounds):
+                mesh.lloyd(1, sp.steps)
+                units_plain += mesh.stats()["skeleton_total"]
+            if sp.dual:
+                mesh.extract_dual()
+            mesh.labels()
     t_plain = time.perf_counter() - t1
     line = {
         "metric": METRIC, "value": units / wall, "unit": UNIT, "n_gpus": 1, "steps": len(trace), "warmup": 0,
@@ -526,8 +532,10 @@ def run_serve(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serve", "jobs": len(trace), "arrival_rate_per_s": 200.0,
                    "last_arrival_s": trace[-1].arrival, "hbm_budget_bytes": 150_000_000_000,
+                   "lloyd_and_dual_jobs": sum(sp.lloyd_rounds > 0 for sp in trace),
                    "desc": "first jobs of the Poisson trace (stream 7): n_v log-normal in [5k, 2M], icosphere / "
-                           "torus / grid, k log-uniform 16-8192, steps U{500..3000}; a step of this line is one job"},
+                           "torus / grid, k log-uniform 16-8192, steps U{500..3000}; half the jobs (stream 8) add 5 "
+                           "Lloyd-like rounds and the dual mesh; a step of this line is one job"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "jobs_per_s": len(trace) / wall,
         "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": (units / wall) / (units_plain / t_plain),

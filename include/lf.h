@@ -332,9 +332,11 @@ lf_status lf_extract_dual(lf_mesh m, int32_t* tris, int64_t cap, int64_t* n_tris
  * stay within hbm_budget_bytes (a job larger than the whole budget fails with
  * LF_ERR_OOM), creates and seeds each one (lf_create_mesh, lf_seed), and
  * advances all running jobs together with lf_step_batch in chunks of
- * chunk_steps.  A job that has taken its n_iters steps gets its sharp labels
- * (Sec. 6) copied to the host and its device memory freed; admission then
- * runs again.  A job that fails (e.g. a vertex summing to zero) is retired
+ * chunk_steps.  A job asking for Lloyd-like rounds (Sec. 5) gets, each time it
+ * has taken its n_iters steps, a seed update and a fresh field, and another
+ * n_iters steps in the batches; a job asking for the dual mesh (Sec. 5.2)
+ * gets it at the end.  A finished job gets its sharp labels (Sec. 6) copied
+ * to the host and its device memory freed; admission then runs again.  A job that fails (e.g. a vertex summing to zero) is retired
  * with its status; the others continue.  The paper runs one mesh at a time;
  * this runtime has no counterpart there.
  * ------------------------------------------------------------------------ */
@@ -357,8 +359,11 @@ typedef struct {
   int64_t arrival_ns;        /* CLOCK_MONOTONIC, as given to lf_server_submit            */
   int64_t admit_ns;          /* when the scheduler put the job on the device (0: not yet) */
   int64_t finish_ns;         /* when its labels were on the host (0: not yet)            */
-  uint64_t skeleton_total;   /* nnz-updates of the job                                   */
+  uint64_t skeleton_total;   /* nnz-updates of the job, all rounds                       */
   int64_t device_bytes;      /* device bytes the job held at the end                     */
+  int32_t lloyd_rounds;      /* Lloyd-like rounds asked for                              */
+  int32_t lloyd_done;        /* rounds completed                                         */
+  int64_t dual_triangles;    /* triangles of the dual mesh (-1: not asked for or not yet) */
 } lf_job_info;
 
 typedef struct {
@@ -380,13 +385,16 @@ lf_status lf_server_create(const lf_device* dev, const lf_server_params* sp, lf_
 
 /* Queues one job.  V (n_v x 3 doubles), F (n_f x 3 int32), seeds (k int32),
  * params (NULL: defaults) are caller-owned and copied before the call returns.
- * arrival_ns is the job's arrival time on CLOCK_MONOTONIC (0: now); latency is
- * finish_ns - arrival_ns.  *job_id gets a positive id.  Errors: LF_ERR_INVALID
- * for any input lf_create_mesh or lf_seed would reject, or n_iters < 0;
- * LF_ERR_STATE after lf_server_destroy began. */
+ * The job takes n_iters steps, then lloyd_rounds times a seed update and
+ * n_iters more steps (as lf_lloyd(m, lloyd_rounds, n_iters)), then, with
+ * extract_dual != 0, the dual mesh (as lf_extract_dual).  arrival_ns is the
+ * job's arrival time on CLOCK_MONOTONIC (0: now); latency is finish_ns -
+ * arrival_ns.  *job_id gets a positive id.  Errors: LF_ERR_INVALID for any
+ * input lf_create_mesh or lf_seed would reject, or n_iters or lloyd_rounds
+ * < 0; LF_ERR_STATE after lf_server_destroy began. */
 lf_status lf_server_submit(lf_server s, const double* V, int64_t n_v, const int32_t* F, int64_t n_f,
-                           const int32_t* seeds, int32_t k, int32_t n_iters, const lf_params* params,
-                           int64_t arrival_ns, int64_t* job_id);
+                           const int32_t* seeds, int32_t k, int32_t n_iters, int32_t lloyd_rounds,
+                           int32_t extract_dual, const lf_params* params, int64_t arrival_ns, int64_t* job_id);
 
 /* Waits up to timeout_s seconds (0: just looks) for the job to finish and
  * fills *info.  When it is done and labels is not NULL, its n_v labels are
@@ -396,6 +404,11 @@ lf_status lf_server_submit(lf_server s, const double* V, int64_t n_v, const int3
  * status when it failed, LF_ERR_INVALID for an unknown id. */
 lf_status lf_server_wait(lf_server s, int64_t job_id, double timeout_s, lf_job_info* info, int32_t* labels,
                          int32_t release);
+
+/* The dual mesh of a finished job that asked for it, as lf_extract_dual
+ * (tris NULL: only *n_tris).  Errors: LF_ERR_INVALID (unknown id), LF_ERR_STATE
+ * (not finished, or no dual mesh asked for), LF_ERR_CAPACITY (cap < *n_tris). */
+lf_status lf_server_dual_mesh(lf_server s, int64_t job_id, int32_t* tris, int64_t cap, int64_t* n_tris);
 
 /* Waits up to timeout_s seconds until no job is queued or running.  Returns
  * LF_OK or LF_ERR_TIMEOUT. */

@@ -63,7 +63,8 @@ class lf_job_info(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("n_v", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("steps_done", ctypes.c_int64), ("arrival_ns", ctypes.c_int64),
                 ("admit_ns", ctypes.c_int64), ("finish_ns", ctypes.c_int64), ("skeleton_total", ctypes.c_uint64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("lloyd_rounds", ctypes.c_int32), ("lloyd_done", ctypes.c_int32),
+                ("dual_triangles", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -122,8 +123,10 @@ _lib.lf_server_default_params.argtypes = [ctypes.POINTER(lf_server_params)]
 _lib.lf_server_default_params.restype = None
 _lib.lf_server_create.argtypes = [ctypes.POINTER(lf_device), ctypes.POINTER(lf_server_params), ctypes.POINTER(_P)]
 _lib.lf_server_create.restype = ctypes.c_int
-_lib.lf_server_submit.argtypes = [_P, _P, _i64, _P, _i64, _P, _i32, _i32, ctypes.POINTER(lf_params), _i64,
-                                  ctypes.POINTER(_i64)]
+_lib.lf_server_submit.argtypes = [_P, _P, _i64, _P, _i64, _P, _i32, _i32, _i32, _i32, ctypes.POINTER(lf_params),
+                                  _i64, ctypes.POINTER(_i64)]
+_lib.lf_server_dual_mesh.argtypes = [_P, _i64, _P, _i64, ctypes.POINTER(_i64)]
+_lib.lf_server_dual_mesh.restype = ctypes.c_int
 _lib.lf_server_submit.restype = ctypes.c_int
 _lib.lf_server_wait.argtypes = [_P, _i64, ctypes.c_double, ctypes.POINTER(lf_job_info), _P, _i32]
 _lib.lf_server_wait.restype = ctypes.c_int
@@ -137,7 +140,7 @@ _lib.lf_server_destroy.restype = None
 EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_step", "lf_labels",
             "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
             "lf_step_noalloc", "lf_step_batch", "lf_lloyd", "lf_extract_dual", "lf_server_default_params", "lf_server_create",
-            "lf_server_submit", "lf_server_wait", "lf_server_drain", "lf_server_stats", "lf_server_destroy"]
+            "lf_server_submit", "lf_server_wait", "lf_server_dual_mesh", "lf_server_drain", "lf_server_stats", "lf_server_destroy"]
 
 
 class LFError(RuntimeError):
@@ -387,15 +390,24 @@ def lf_server_create(params=None):
     return out
 
 
-def lf_server_submit(server, V, F, seeds, n_iters, params=None, arrival_ns=0):
+def lf_server_submit(server, V, F, seeds, n_iters, params=None, arrival_ns=0, lloyd_rounds=0, extract_dual=False):
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
     seeds = np.ascontiguousarray(seeds, dtype=np.int32)
     jid = _i64()
     _check(_lib.lf_server_submit(server, _ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(seeds), seeds.size,
-                                 int(n_iters), ctypes.byref(params) if params is not None else None,
+                                 int(n_iters), int(lloyd_rounds), 1 if extract_dual else 0,
+                                 ctypes.byref(params) if params is not None else None,
                                  int(arrival_ns), ctypes.byref(jid)))
     return jid.value
+
+
+def lf_server_dual_mesh(server, job_id):
+    n = _i64()
+    _check(_lib.lf_server_dual_mesh(server, int(job_id), None, 0, ctypes.byref(n)))
+    out = np.empty((n.value, 3), np.int32)
+    _check(_lib.lf_server_dual_mesh(server, int(job_id), _ptr(out), n.value, ctypes.byref(n)))
+    return out
 
 
 def lf_server_wait(server, job_id, timeout_s=0.0, n_v=None, release=False):
@@ -429,10 +441,14 @@ class Server:
     def __init__(self, **overrides):
         self.h = lf_server_create(lf_server_default_params(**overrides))
 
-    def submit(self, V, F, seeds, n_iters, params=None, arrival_ns=0, **overrides):
+    def submit(self, V, F, seeds, n_iters, params=None, arrival_ns=0, lloyd_rounds=0, extract_dual=False,
+               **overrides):
         if params is None and overrides:
             params = lf_default_params(**overrides)
-        return lf_server_submit(self.h, V, F, seeds, n_iters, params, arrival_ns)
+        return lf_server_submit(self.h, V, F, seeds, n_iters, params, arrival_ns, lloyd_rounds, extract_dual)
+
+    def dual_mesh(self, job_id):
+        return lf_server_dual_mesh(self.h, job_id)
 
     def wait(self, job_id, timeout_s=0.0, n_v=None, release=False):
         return lf_server_wait(self.h, job_id, timeout_s, n_v, release)

@@ -536,6 +536,27 @@ bool seeds_ok(int64_t n_v, const int32_t* seeds, int32_t k, std::string& why) {
 
 bool params_valid(const lf_params& p, std::string& why) { return params_ok(p, why); }
 
+lf_status attach_geometry(lf_mesh m, const double* V, int64_t n_v, const int32_t* F, int64_t n_f) {
+  if (n_v != m->n_v) return fail(m, LF_ERR_INVALID, "geometry does not match the mesh");
+  m->d_V = static_cast<double*>(m->dalloc(sizeof(double) * 3 * static_cast<size_t>(n_v)));
+  m->d_tri = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * 3 * static_cast<size_t>(n_f)));
+  if (!m->d_V || !m->d_tri) return fail(m, LF_ERR_OOM, "uploading the mesh");
+  LF_CUDA(m, cudaMemcpyAsync(m->d_V, V, sizeof(double) * 3 * n_v, cudaMemcpyHostToDevice, m->stream));
+  LF_CUDA(m, cudaMemcpyAsync(m->d_tri, F, sizeof(int32_t) * 3 * n_f, cudaMemcpyHostToDevice, m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  m->n_f = n_f;
+  return LF_OK;
+}
+
+int64_t geometry_bytes_estimate(int64_t n_v, int64_t n_f, int64_t k) {
+  auto r = [](int64_t b) { return (std::max<int64_t>(b, 16) + 255) & ~int64_t(255); };
+  int64_t tab = 4096;
+  while (tab < 16 * k) tab <<= 1;
+  return r(24 * n_v) + r(12 * n_f) +                              // V, faces
+         r(56 * k) * 2 + r(16 * k) + r(8 * n_v) + 3 * r(4 * k) +  // Lloyd scratch and seeds
+         4 * r(4 * tab) + r(4 * n_v) + 2 * r(24 * k);              // dual scratch
+}
+
 lf_status create_from_offdiag(const lf_device* dev, int64_t n_v, const std::vector<int64_t>& rp,
                               const std::vector<int32_t>& col, const std::vector<double>& val,
                               const lf_params& prm, lf_mesh* out) {
@@ -593,23 +614,13 @@ lf_status lf_create_mesh(const lf_device* dev, const double* V, int64_t n_v, con
   lf_status s = finish_create(dev, n_v, rp, col, val, prm, out);
   if (s != LF_OK) return s;
   // the mesh itself stays on the device for the Lloyd-like update (Sec. 5)
-  lf_mesh m = *out;
-  m->d_V = static_cast<double*>(m->dalloc(sizeof(double) * 3 * static_cast<size_t>(n_v)));
-  m->d_tri = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * 3 * static_cast<size_t>(n_f)));
-  cudaError_t e = (m->d_V && m->d_tri) ? cudaSuccess : cudaErrorMemoryAllocation;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(m->d_V, V, sizeof(double) * 3 * n_v, cudaMemcpyHostToDevice, m->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(m->d_tri, F, sizeof(int32_t) * 3 * n_f, cudaMemcpyHostToDevice, m->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    delete m;
+  s = lf::attach_geometry(*out, V, n_v, F, n_f);
+  if (s != LF_OK) {
+    g_create_error = (*out)->err;
+    delete *out;
     *out = nullptr;
-    return fail(nullptr, e == cudaErrorMemoryAllocation ? LF_ERR_OOM : LF_ERR_CUDA, "uploading the mesh");
   }
-  m->n_f = n_f;
-  return LF_OK;
+  return s;
 }
 
 lf_status lf_create_mesh_csr(const lf_device* dev, int64_t n_v, const int64_t* rowptr, const int32_t* col,

@@ -157,6 +157,11 @@ bool params_valid(const lf_params& p, std::string& why);
 lf_status create_from_offdiag(const lf_device* dev, int64_t n_v, const std::vector<int64_t>& rp,
                               const std::vector<int32_t>& col, const std::vector<double>& val,
                               const lf_params& prm, lf_mesh* out);
+// Uploads a mesh's vertices and faces (the Lloyd-like update and the dual
+// mesh need them).
+lf_status attach_geometry(lf_mesh m, const double* V, int64_t n_v, const int32_t* F, int64_t n_f);
+// Device bytes the geometry, the Lloyd scratch and the dual-mesh scratch add.
+int64_t geometry_bytes_estimate(int64_t n_v, int64_t n_f, int64_t k);
 // Device bytes lf_create_mesh would allocate for this operator and parameters.
 int64_t device_bytes_estimate(int64_t n_v, int64_t nnz_off, const lf_params& prm);
 

@@ -40,7 +40,14 @@ struct Job {
   std::vector<int32_t> col;
   std::vector<double> val;
   std::vector<int32_t> seeds;
+  std::vector<double> V;            // geometry, kept only for Lloyd rounds or the dual mesh
+  std::vector<int32_t> F;
   int32_t n_iters = 0;
+  int32_t lloyd_rounds = 0, lloyd_done = 0;
+  bool want_dual = false;
+  std::vector<int32_t> dual;        // oriented triangles, 3 seed ids each
+  bool dual_ready = false;
+  uint64_t skeleton_before = 0;     // nnz-updates of the finished rounds
   lf_params prm{};
   int64_t bytes_est = 0;
   int64_t arrival_ns = 0, admit_ns = 0, finish_ns = 0;
@@ -140,10 +147,14 @@ void scheduler(lf_server_s* s) {
     for (const JobPtr& j : admit) {
       lf_mesh m = nullptr;
       lf_status r = lf::create_from_offdiag(&s->dev, j->n_v, j->rp, j->col, j->val, j->prm, &m);
+      if (r == LF_OK && !j->V.empty())
+        r = lf::attach_geometry(m, j->V.data(), j->n_v, j->F.data(), static_cast<int64_t>(j->F.size() / 3));
       if (r == LF_OK) r = lf_seed(m, j->seeds.data(), static_cast<int32_t>(j->seeds.size()));
       std::vector<int64_t>().swap(j->rp);
       std::vector<int32_t>().swap(j->col);
       std::vector<double>().swap(j->val);
+      std::vector<double>().swap(j->V);
+      std::vector<int32_t>().swap(j->F);
       std::lock_guard<std::mutex> lk(s->mu);
       j->mesh = m;
       j->admit_ns = now_ns();
@@ -193,14 +204,42 @@ void scheduler(lf_server_s* s) {
       if (rs == LF_OK) {
         std::lock_guard<std::mutex> lk(s->mu);
         j->steps_done = stt.steps;
-        j->skeleton_total = stt.skeleton_total;
+        j->skeleton_total = j->skeleton_before + stt.skeleton_total;
         j->device_bytes = stt.device_bytes;
       }
       if (rs != LF_OK || (r != LF_OK && j->steps_done < before[a] + cnt[a])) {
         retire(s, j, LF_JOB_FAILED, rs != LF_OK ? rs : r);
         continue;
       }
+      if (j->steps_done >= j->n_iters && j->lloyd_done < j->lloyd_rounds) {
+        // a Lloyd-like round: new seeds and a fresh field; the round's steps
+        // then run in the following batches
+        const uint64_t sk = j->skeleton_total;
+        rs = lf_lloyd(j->mesh, 1, 0, nullptr);
+        if (rs != LF_OK) {
+          retire(s, j, LF_JOB_FAILED, rs);
+          continue;
+        }
+        std::lock_guard<std::mutex> lk(s->mu);
+        j->skeleton_before = sk;
+        j->steps_done = 0;
+        ++j->lloyd_done;
+        continue;
+      }
       if (j->steps_done >= j->n_iters) {
+        if (j->want_dual) {
+          int64_t n = 0;
+          rs = lf_extract_dual(j->mesh, nullptr, 0, &n);
+          std::vector<int32_t> tris(static_cast<size_t>(3 * n));
+          if (rs == LF_OK && n > 0) rs = lf_extract_dual(j->mesh, tris.data(), n, &n);
+          if (rs != LF_OK) {
+            retire(s, j, LF_JOB_FAILED, rs);
+            continue;
+          }
+          std::lock_guard<std::mutex> lk(s->mu);
+          j->dual.swap(tris);
+          j->dual_ready = true;
+        }
         std::vector<int32_t> lab(static_cast<size_t>(j->n_v));
         rs = lf_labels(j->mesh, lab.data(), nullptr);
         if (rs == LF_OK) {
@@ -243,6 +282,9 @@ void fill_info(const Job& j, lf_job_info* info) {
   info->finish_ns = j.finish_ns;
   info->skeleton_total = j.skeleton_total;
   info->device_bytes = j.device_bytes;
+  info->lloyd_rounds = j.lloyd_rounds;
+  info->lloyd_done = j.lloyd_done;
+  info->dual_triangles = j.dual_ready ? static_cast<int64_t>(j.dual.size() / 3) : -1;
 }
 
 bool finished(const Job& j) { return j.state == LF_JOB_DONE || j.state == LF_JOB_FAILED; }
@@ -297,8 +339,8 @@ lf_status lf_server_create(const lf_device* dev, const lf_server_params* sp, lf_
 }
 
 lf_status lf_server_submit(lf_server s, const double* V, int64_t n_v, const int32_t* F, int64_t n_f,
-                           const int32_t* seeds, int32_t k, int32_t n_iters, const lf_params* params,
-                           int64_t arrival_ns, int64_t* job_id) {
+                           const int32_t* seeds, int32_t k, int32_t n_iters, int32_t lloyd_rounds,
+                           int32_t extract_dual, const lf_params* params, int64_t arrival_ns, int64_t* job_id) {
   if (!s || !job_id) return server_fail(LF_ERR_INVALID, "null server or job_id");
   lf_params prm;
   lf_default_params(&prm);
@@ -306,18 +348,25 @@ lf_status lf_server_submit(lf_server s, const double* V, int64_t n_v, const int3
   std::string why;
   if (!lf::params_valid(prm, why) || !lf::mesh_ok(n_v, V, n_f, F, why) || !lf::seeds_ok(n_v, seeds, k, why))
     return server_fail(LF_ERR_INVALID, why);
-  if (n_iters < 0) return server_fail(LF_ERR_INVALID, "n_iters must be >= 0");
+  if (n_iters < 0 || lloyd_rounds < 0) return server_fail(LF_ERR_INVALID, "n_iters and lloyd_rounds must be >= 0");
   auto j = std::make_shared<Job>();
   try {
     if (!lf::cotan_offdiag(n_v, V, n_f, F, j->rp, j->col, j->val, why)) return server_fail(LF_ERR_INVALID, why);
     j->seeds.assign(seeds, seeds + k);
+    if (lloyd_rounds > 0 || extract_dual) {
+      j->V.assign(V, V + 3 * n_v);
+      j->F.assign(F, F + 3 * n_f);
+    }
   } catch (const std::bad_alloc&) {
     return server_fail(LF_ERR_OOM, "host allocation");
   }
   j->n_v = n_v;
   j->n_iters = n_iters;
+  j->lloyd_rounds = lloyd_rounds;
+  j->want_dual = extract_dual != 0;
   j->prm = prm;
   j->bytes_est = lf::device_bytes_estimate(n_v, static_cast<int64_t>(j->col.size()), prm);
+  if (!j->V.empty()) j->bytes_est += lf::geometry_bytes_estimate(n_v, n_f, k);
   j->arrival_ns = arrival_ns > 0 ? arrival_ns : now_ns();
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -350,6 +399,21 @@ lf_status lf_server_wait(lf_server s, int64_t job_id, double timeout_s, lf_job_i
   const lf_status r = j->state == LF_JOB_DONE ? LF_OK : static_cast<lf_status>(j->status);
   if (release) s->jobs.erase(job_id);
   return r;
+}
+
+lf_status lf_server_dual_mesh(lf_server s, int64_t job_id, int32_t* tris, int64_t cap, int64_t* n_tris) {
+  if (!s || !n_tris) return server_fail(LF_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return server_fail(LF_ERR_INVALID, "unknown job id");
+  const Job& j = *it->second;
+  if (!j.dual_ready) return server_fail(LF_ERR_STATE, "no dual mesh for this job (not asked for, or not finished)");
+  const int64_t n = static_cast<int64_t>(j.dual.size() / 3);
+  *n_tris = n;
+  if (!tris) return LF_OK;
+  if (cap < n) return server_fail(LF_ERR_CAPACITY, "tris holds fewer than *n_tris triangles");
+  if (n > 0) std::memcpy(tris, j.dual.data(), sizeof(int32_t) * 3 * static_cast<size_t>(n));
+  return LF_OK;
 }
 
 lf_status lf_server_drain(lf_server s, double timeout_s) {

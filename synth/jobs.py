@@ -13,7 +13,8 @@ serve_trace: Poisson arrivals at `rate` jobs/s until `n_jobs` jobs or
 `duration` seconds; n_v log-normal with median sqrt(5k * 2M) whose +-2.326
 sigma range is [5k, 2M], clipped to it; kind uniform over icosphere, torus
 and grid; k log-uniform in [16, 8192] (at most n_v / 4); steps uniform in
-{500, ..., 3000}.
+{500, ..., 3000}; with probability 1/2 (a stream of its own, seed + 1) the job
+also asks for 5 Lloyd-like rounds and the dual mesh.
 """
 import math
 from dataclasses import dataclass
@@ -35,6 +36,8 @@ class JobSpec:
     steps: int
     seed_stream: int     # stream of the seed vertices
     arrival: float = 0.0 # seconds from the start of the trace
+    lloyd_rounds: int = 0
+    dual: bool = False
 
     @property
     def n_v(self):
@@ -67,6 +70,7 @@ def batch_mix(n_jobs=64, seed=6, steps=1000, nv_range=(10_000, 600_000), k_range
 def serve_trace(n_jobs=2000, seed=7, rate=200.0, duration=60.0, nv_range=(5_000, 2_000_000),
                 k_range=(16, 8192), steps_range=(500, 3000)):
     u = uniform01(seed, np.arange(6 * n_jobs, dtype=np.uint64)).reshape(n_jobs, 6)
+    extra = uniform01(seed + 1, np.arange(n_jobs, dtype=np.uint64))
     median = math.sqrt(nv_range[0] * nv_range[1])
     sigma = math.log(nv_range[1] / nv_range[0]) / (2 * 2.326)
     jobs, t = [], 0.0
@@ -82,7 +86,8 @@ def serve_trace(n_jobs=2000, seed=7, rate=200.0, duration=60.0, nv_range=(5_000,
         spec_nv = 10 * 4 ** size + 2 if kind == "ico" else size * size
         k = min(int(round(_log_uniform(u[i, 4], *k_range))), spec_nv // 4)
         steps = steps_range[0] + min(steps_range[1] - steps_range[0], int(u[i, 5] * (steps_range[1] - steps_range[0] + 1)))
-        jobs.append(JobSpec(kind, size, k, "f32", steps, 2000 + i, t))
+        full = extra[i] < 0.5
+        jobs.append(JobSpec(kind, size, k, "f32", steps, 2000 + i, t, 5 if full else 0, full))
     return jobs
 
 

@@ -144,3 +144,36 @@ def test_server_timeouts_and_invalid_calls(lf):
     t0 = time.monotonic()
     srv.close()
     assert time.monotonic() - t0 < 30.0
+
+
+def test_server_lloyd_rounds_and_dual_mesh_match_the_job_alone(lf):
+    # two jobs asking for Lloyd-like rounds and the dual mesh, batched with a
+    # plain one: seeds, labels and triangles equal those of the same calls
+    # on the job alone (lf_step, lf_lloyd, lf_extract_dual)
+    jobs = [(synth.planar_grid(41, seed=3), 16, 1, 120, 2, True), (synth.noisy_torus(40), 24, 5, 150, 1, True),
+            (synth.planar_grid(33, seed=7), 24, 9, 90, 0, False)]
+    with lf.Server(chunk_steps=50) as srv:
+        ids = [srv.submit(m.V, m.F, synth.sample_seeds(m.n_v, k, sid), n, lloyd_rounds=r, extract_dual=d)
+               for m, k, sid, n, r, d in jobs]
+        assert srv.drain(120.0) == lf.LF_OK
+        for jid, (m, k, sid, n, r, d) in zip(ids, jobs):
+            status, info, labels = srv.wait(jid, 0.0, n_v=m.n_v)
+            assert status == lf.LF_OK and info["lloyd_done"] == r == info["lloyd_rounds"]
+            with lf.Mesh(m.V, m.F) as mesh:
+                mesh.seed(synth.sample_seeds(m.n_v, k, sid))
+                mesh.step(n)
+                total = mesh.stats()["skeleton_total"]
+                for _ in range(r):
+                    mesh.lloyd(1, n)
+                    total += mesh.stats()["skeleton_total"]
+                assert np.array_equal(labels, mesh.labels())
+                assert info["skeleton_total"] == total
+                if d:
+                    tri = srv.dual_mesh(jid)
+                    assert info["dual_triangles"] == len(tri) > 0
+                    assert np.array_equal(tri, mesh.extract_dual())
+                else:
+                    assert info["dual_triangles"] == -1
+                    with pytest.raises(lf.LFError) as ei:
+                        srv.dual_mesh(jid)
+                    assert ei.value.status == lf.LF_ERR_STATE
