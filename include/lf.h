@@ -154,6 +154,37 @@ lf_status lf_create_mesh_csr(const lf_device* dev, int64_t n_v, const int64_t* r
 lf_status lf_seed(lf_mesh m, const int32_t* seed_vertices, int32_t k);
 
 /*
+ * Region seeds (Sec. 3.2, "Initialization": a vertex and its immediate
+ * neighbours set to 1).  rings = 0 is lf_seed; rings = 1 gives layer c to seed
+ * vertex seeds[c] and to its neighbours in L.  A vertex reached by several
+ * seeds keeps its own seed's layer if it is a seed, else takes the lowest
+ * seed id; every other vertex holds the base layer.  Seeds are remembered as
+ * for lf_seed.  Errors: as lf_seed, and LF_ERR_INVALID for rings outside [0, 1].
+ */
+lf_status lf_seed_regions(lf_mesh m, const int32_t* seeds, int32_t k, int32_t rings);
+
+/*
+ * General coefficient matrices of Algorithm 1 (Sec. 3.3 states the update
+ * for any w_jl, a_jl, e_jk; Sec. 3.4 picks the class values that lf_params
+ * holds).  W, A and E are host pointers, each NULL or an n_layers x n_layers
+ * row-major FP32 matrix indexed by layer id (cells 0..k-1, base layer k):
+ * W[j * n_layers + l] = w_jl, A[...] = a_jl, E[j * n_layers + k] = e_jk.  A
+ * NULL matrix keeps the class rule for that coefficient; all three NULL
+ * returns to the class coefficients.  Every entry is used as given, diagonal
+ * included, with no symmetry assumed.  The library copies the matrices to
+ * the device (n_layers^2 * 4 bytes each) and the call returns after the
+ * copy.  They hold until the next call, or until the field takes another
+ * layer count (lf_seed or lf_set_field with a different k); seeding again
+ * with the same k, as lf_lloyd does, keeps them.  A mesh with matrices runs
+ * the general form of the step kernel, which sums the matrices over the
+ * skeleton of each vertex.
+ * Errors: LF_ERR_STATE before the first lf_seed / lf_set_field;
+ * LF_ERR_INVALID if n_layers differs from the field's layer count, exceeds
+ * 4096, or an entry is not finite; LF_ERR_OOM.
+ */
+lf_status lf_set_coefficients(lf_mesh m, int32_t n_layers, const float* W, const float* A, const float* E);
+
+/*
  * Runs n_iters time-iterations of Algorithm 1 (the body of its time loop):
  * L_t = L F (the paper's Phi L^T for a symmetric L), the interest skeleton
  * irows_i = {l : F_il > 0} u {l : F_il = 0, (L F)_il > 0}, the explicit Euler

@@ -11,6 +11,7 @@ on Surfaces" (arXiv 1804.09152), cited in the C source:
 
 * ``cotan_laplacian`` -- the precomputed mesh Laplacian (Sec. 3.2),
 * ``seed``            -- initialisation with seeds and the base layer (Sec. 3.1, 3.2),
+* ``seed_regions``    -- the same with a seed's immediate neighbours (Sec. 3.2),
 * ``lt``              -- the product L_t = Phi L^T of Algorithm 1 (Sec. 4),
 * ``step``            -- one time-iteration of Algorithm 1 (Eq. 11-13, Sec. 4),
 * ``step_closed``     -- the same update through its closed form for the
@@ -168,6 +169,31 @@ def seed(n_v, seeds):
     if rc != 0:
         raise ValueError(f"orc_seed failed ({rc})")
     return Field(rp, ids, vals, k + 1)
+
+
+def seed_regions(L, seeds, rings=1):
+    """Initial field with region seeds (Sec. 3.2, "Initialization": a vertex
+    and its immediate neighbours set to 1).  Layer c goes to seed vertex
+    seeds[c] and, with rings = 1, to its neighbours in L; a vertex reached by
+    several seeds keeps its own seed's layer if it is a seed, else takes the
+    lowest seed id; all other vertices hold the base layer k."""
+    seeds = [int(x) for x in seeds]
+    k = len(seeds)
+    n_v = L.rowptr.size - 1
+    owner = [None] * n_v
+    seed_set = set(seeds)
+    for c, v in enumerate(seeds):
+        owner[v] = c                                   # seed vertices first
+    if rings == 1:
+        for c, v in enumerate(seeds):
+            for q in range(L.rowptr[v], L.rowptr[v + 1]):
+                j = int(L.col[q])
+                if j == v or j in seed_set:
+                    continue
+                if owner[j] is None or c < owner[j]:
+                    owner[j] = c
+    ids = np.array([k if o is None else o for o in owner], np.int32)
+    return Field(np.arange(n_v + 1, dtype=np.int64), ids, np.ones(n_v), k + 1)
 
 
 def _coefs(params):

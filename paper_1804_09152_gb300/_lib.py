@@ -92,6 +92,10 @@ _lib.lf_create_mesh.restype = ctypes.c_int
 _lib.lf_create_mesh_csr.argtypes = [ctypes.POINTER(lf_device), _i64, _P, _P, _P, ctypes.POINTER(lf_params),
                                     ctypes.POINTER(_P)]
 _lib.lf_create_mesh_csr.restype = ctypes.c_int
+_lib.lf_seed_regions.argtypes = [_P, _P, _i32, _i32]
+_lib.lf_seed_regions.restype = ctypes.c_int
+_lib.lf_set_coefficients.argtypes = [_P, _i32, _P, _P, _P]
+_lib.lf_set_coefficients.restype = ctypes.c_int
 _lib.lf_seed.argtypes = [_P, _P, _i32]
 _lib.lf_seed.restype = ctypes.c_int
 _lib.lf_step.argtypes = [_P, _i32]
@@ -137,7 +141,8 @@ _lib.lf_server_stats.restype = ctypes.c_int
 _lib.lf_server_destroy.argtypes = [_P]
 _lib.lf_server_destroy.restype = None
 
-EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_step", "lf_labels",
+EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_seed_regions",
+            "lf_set_coefficients", "lf_step", "lf_labels",
             "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
             "lf_step_noalloc", "lf_step_batch", "lf_lloyd", "lf_extract_dual", "lf_server_default_params", "lf_server_create",
             "lf_server_submit", "lf_server_wait", "lf_server_dual_mesh", "lf_server_drain", "lf_server_stats", "lf_server_destroy"]
@@ -219,6 +224,26 @@ def lf_create_mesh_csr(rowptr, col, val, params=None, device=None):
 def lf_seed(mesh, seeds):
     seeds = np.ascontiguousarray(seeds, dtype=np.int32)
     _check(_lib.lf_seed(mesh, _ptr(seeds), seeds.size), mesh)
+
+
+def lf_seed_regions(mesh, seeds, rings):
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    _check(_lib.lf_seed_regions(mesh, _ptr(seeds), seeds.size, int(rings)), mesh)
+
+
+def lf_set_coefficients(mesh, n_layers, W=None, A=None, E=None):
+    """Dense FP32 coefficient matrices (None: class rule for that one)."""
+    mats = []
+    for M in (W, A, E):
+        if M is None:
+            mats.append(None)
+            continue
+        M = np.ascontiguousarray(M, dtype=np.float32)
+        if M.shape != (n_layers, n_layers):
+            raise ValueError(f"coefficient matrix must be {n_layers}x{n_layers}, got {M.shape}")
+        mats.append(M)
+    ptrs = [None if M is None else _ptr(M) for M in mats]
+    _check(_lib.lf_set_coefficients(mesh, int(n_layers), *ptrs), mesh)
 
 
 def lf_step(mesh, n_iters):
@@ -334,6 +359,13 @@ class Mesh:
 
     def seed(self, seeds):
         lf_seed(self.h, seeds)
+
+    def seed_regions(self, seeds, rings=1):
+        lf_seed_regions(self.h, seeds, rings)
+
+    def set_coefficients(self, W=None, A=None, E=None):
+        n = self.stats()["n_layers"]
+        lf_set_coefficients(self.h, n, W, A, E)
 
     def step(self, n):
         lf_step(self.h, n)

@@ -27,6 +27,7 @@ thread_local std::string g_create_error;
 constexpr int kGraphSteps = 128;     // kernel nodes per captured graph
 constexpr int kPollSteps = 512;      // steps between status checks in lf_step
 constexpr int64_t kMaxCap = 2147483000LL;
+constexpr int kMaxCoefLayers = 4096;  // dense coefficient matrices: at most 64 MiB each
 
 struct Alloc {
   void* p;
@@ -63,6 +64,11 @@ struct lf_mesh_s {
   int64_t scratch_f_len = 0;
 
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // step graphs by starting parity
+
+  // general coefficient matrices (lf_set_coefficients): one device block of
+  // up to three n_layers x n_layers FP32 matrices for that layer count
+  float* d_coef = nullptr;
+  int coef_layers = 0;
 
   // geometry (lf_create_mesh only) and seeds, for the Lloyd-like update
   double* d_V = nullptr;         // n_v x 3
@@ -375,7 +381,7 @@ cudaError_t make_step_graph(const std::vector<std::pair<int, lf::BatchParams>>& 
       params.back().step = s;
       void* args[1] = {&params.back()};
       cudaKernelNodeParams kp{};
-      kp.func = const_cast<void*>(lf::step_kernel(dtype));
+      kp.func = const_cast<void*>(lf::step_kernel(dtype, lf::needs_general(chains[c].second)));
       kp.gridDim = dim3(static_cast<unsigned>(chains[c].second.tile_start[chains[c].second.n_jobs]));
       kp.blockDim = dim3(static_cast<unsigned>(lf::kTile));
       kp.sharedMemBytes = 0;
@@ -655,29 +661,106 @@ lf_status lf_create_mesh_csr(const lf_device* dev, int64_t n_v, const int64_t* r
   return finish_create(dev, n_v, rp, c2, v2, prm, out);
 }
 
-lf_status lf_seed(lf_mesh m, const int32_t* seeds, int32_t k) {
+}  // extern "C"
+
+namespace {
+
+// Coefficient matrices hold for one layer count: a field with another count
+// (new seeds, lf_set_field) returns the mesh to the class coefficients.
+void drop_coefficients(lf_mesh m, bool always) {
+  if (!m->d_coef || (!always && m->coef_layers == m->n_layers)) return;
+  m->dfree(m->d_coef);
+  m->d_coef = nullptr;
+  m->coef_layers = 0;
+  m->h_job.cW = m->h_job.cA = m->h_job.cE = nullptr;
+  upload_job(m);
+}
+
+// Initial field (Sec. 3.2): point seeds (rings = 0) or a seed vertex with its
+// immediate neighbours (rings = 1); every other vertex holds the base layer.
+lf_status seed_impl(lf_mesh m, const int32_t* seeds, int32_t k, int32_t rings) {
   lf_status s = check_usable(m);
   if (s != LF_OK) return s;
+  if (rings < 0 || rings > 1) return fail(m, LF_ERR_INVALID, "rings must be 0 or 1");
   std::string why;
   if (!lf::seeds_ok(m->n_v, seeds, k, why)) return fail(m, LF_ERR_INVALID, why);
   auto* d_seeds = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * static_cast<size_t>(k)));
   if (!d_seeds) return fail(m, LF_ERR_OOM, "seed upload buffer");
+  unsigned* d_owner = nullptr;
+  if (rings == 1) {
+    d_owner = static_cast<unsigned*>(m->dalloc(sizeof(unsigned) * static_cast<size_t>(m->n_v)));
+    if (!d_owner) {
+      m->dfree(d_seeds);
+      return fail(m, LF_ERR_OOM, "region seed scratch");
+    }
+  }
   m->n_layers = k + 1;
   m->h_job.n_layers = k + 1;
+  drop_coefficients(m, false);
   std::memset(&m->h_st, 0, sizeof(m->h_st));
   m->h_st.nnz = static_cast<unsigned long long>(m->n_v);
   s = upload_job(m);
   if (s == LF_OK) s = upload_status(m);
   if (s != LF_OK) return s;
   LF_CUDA(m, cudaMemcpyAsync(d_seeds, seeds, sizeof(int32_t) * k, cudaMemcpyHostToDevice, m->stream));
-  LF_CUDA(m, lf::launch_seed(m->h_job, k, d_seeds, m->dtype, m->stream));
+  if (rings == 1) {
+    LF_CUDA(m, lf::launch_seed_regions(m->h_job, k, d_seeds, d_owner, m->dtype, m->stream));
+  } else {
+    LF_CUDA(m, lf::launch_seed(m->h_job, k, d_seeds, m->dtype, m->stream));
+  }
   LF_CUDA(m, cudaStreamSynchronize(m->stream));
   m->dfree(d_seeds);
+  m->dfree(d_owner);
   m->steps = 0;
   m->retries = 0;
   m->seeds.assign(seeds, seeds + k);
   ++m->version;
   return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lf_status lf_seed(lf_mesh m, const int32_t* seeds, int32_t k) { return seed_impl(m, seeds, k, 0); }
+
+lf_status lf_seed_regions(lf_mesh m, const int32_t* seeds, int32_t k, int32_t rings) {
+  return seed_impl(m, seeds, k, rings);
+}
+
+lf_status lf_set_coefficients(lf_mesh m, int32_t n_layers, const float* W, const float* A, const float* E) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed or lf_set_field must come first");
+  if (n_layers != m->n_layers) return fail(m, LF_ERR_INVALID, "n_layers differs from the field's layer count");
+  if (n_layers > kMaxCoefLayers) return fail(m, LF_ERR_INVALID, "coefficient matrices take at most 4096 layers");
+  const float* src[3] = {W, A, E};
+  const int64_t nn = static_cast<int64_t>(n_layers) * n_layers;
+  int present = 0;
+  for (const float* M : src) {
+    if (!M) continue;
+    ++present;
+    for (int64_t q = 0; q < nn; ++q)
+      if (!std::isfinite(M[q])) return fail(m, LF_ERR_INVALID, "coefficient matrices must be finite");
+  }
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));   // no step in flight reads the old block
+  drop_coefficients(m, true);
+  if (present == 0) return LF_OK;
+  auto* d = static_cast<float*>(m->dalloc(sizeof(float) * static_cast<size_t>(nn * present)));
+  if (!d) return fail(m, LF_ERR_OOM, "coefficient matrices");
+  const float** dst[3] = {&m->h_job.cW, &m->h_job.cA, &m->h_job.cE};
+  int slot = 0;
+  for (int x = 0; x < 3; ++x) {
+    if (!src[x]) continue;
+    float* part = d + static_cast<int64_t>(slot++) * nn;
+    LF_CUDA(m, cudaMemcpyAsync(part, src[x], sizeof(float) * static_cast<size_t>(nn), cudaMemcpyHostToDevice,
+                               m->stream));
+    *dst[x] = part;
+  }
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  m->d_coef = d;
+  m->coef_layers = n_layers;
+  return upload_job(m);
 }
 
 lf_status lf_step(lf_mesh m, int32_t n_iters) {
@@ -986,6 +1069,7 @@ lf_status lf_set_field(lf_mesh m, const int64_t* rowptr, const int32_t* layer, c
   LF_CUDA(m, lf::launch_build_head(m->buf[cur], static_cast<int>(m->n_v), m->dtype, m->stream));
   m->n_layers = n_layers;
   m->h_job.n_layers = n_layers;
+  drop_coefficients(m, false);
   m->h_st.nnz = static_cast<unsigned long long>(nnz);
   if (static_cast<int64_t>(m->seeds.size()) != n_layers - 1) m->seeds.clear();
   ++m->version;

@@ -69,6 +69,11 @@ struct JobDesc {
   const int2* L_colval;      // (column, float bits of L_ij), j != i
   FieldBuf buf[2];
   DevStatus* st;
+  // General coefficient matrices (Algorithm 1's w_jl, a_jl, e_jk), dense
+  // n_layers x n_layers row-major FP32; null: the class coefficients in c.
+  const float* cW;
+  const float* cA;
+  const float* cE;
   Coefs c;
   int32_t pad;
 };
@@ -89,15 +94,22 @@ constexpr int kTile = 256;   // vertices per tile = threads per step CTA
 
 // Register slots of the step kernel's fast path.
 int step_slots();
-// Kernel entry of the step for a storage type (0 f32, 1 bf16, 2 f16); its
-// only argument is a BatchParams.
-const void* step_kernel(int dtype);
+// Kernel entry of the step for a storage type (0 f32, 1 bf16, 2 f16), in
+// the form for general coefficient matrices or not; its only argument is a
+// BatchParams.
+const void* step_kernel(int dtype, bool general);
+// True when a job of the launch has general coefficient matrices.
+bool needs_general(const BatchParams& p);
 // One step launch over the jobs in p, with programmatic stream serialisation.
 cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s);
 // The seed and label kernels take one job by value.
 cudaError_t launch_seed(const JobDesc& job, int k, const int32_t* d_seeds, int dtype, cudaStream_t s);
 cudaError_t launch_labels(const JobDesc& job, int buf, int dtype, int32_t* d_labels, float* d_maxval,
                           cudaStream_t s);
+// Region seeds: each seed vertex and its neighbours in L take the seed's
+// layer (own seed first, else the lowest seed id); d_owner is n_v scratch.
+cudaError_t launch_seed_regions(const JobDesc& job, int k, const int32_t* d_seeds, unsigned* d_owner, int dtype,
+                                cudaStream_t s);
 // head[] of a field buffer from its rows, ids and vals.
 cudaError_t launch_build_head(const FieldBuf& b, int n_v, int dtype, cudaStream_t s);
 // Copies the rows of `from` into the segments of `to` (tile_cap may differ).

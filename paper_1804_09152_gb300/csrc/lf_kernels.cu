@@ -147,6 +147,45 @@ struct Update {
   }
 };
 
+// Algorithm 1 with general coefficient matrices (w_jl, a_jl, e_jk): with
+// A_j = sum_l a_jl G_l, W_j = sum_l w_jl F_l, E_j = sum_k e_jk sqrt(F_k) over
+// the skeleton S (n entries), d_j = -(mu/n)[1/2 (n A_j - sum_S A) +
+// (n W_j - sum_S W)] + (mu/n) sqrt(F_j) E_j.  A missing matrix falls back to
+// the class rule of the coefficients.  Every sum runs in ascending layer
+// order with explicit roundings, the same in every tier.
+struct GenCoef {
+  const float* W;
+  const float* A;
+  const float* E;
+  int K1, base;
+  Coefs c;
+  __device__ __forceinline__ float w(int j, int l) const {
+    if (W) return __ldg(W + static_cast<int64_t>(j) * K1 + l);
+    return j == l ? 0.0f : ((j == base || l == base) ? c.w_cb : c.w_cc);
+  }
+  __device__ __forceinline__ float a(int j, int l) const {
+    if (A) return __ldg(A + static_cast<int64_t>(j) * K1 + l);
+    return j == l ? 0.0f : ((j == base || l == base) ? c.a_cb : c.a_cc);
+  }
+  __device__ __forceinline__ float e(int j, int k) const {
+    if (E) return __ldg(E + static_cast<int64_t>(j) * K1 + k);
+    if (j == k) return 0.0f;
+    if (j == base) return c.e_bc;
+    return k == base ? c.e_cb : c.e_cc;
+  }
+  // value of entry j from its A_j, W_j, E_j and the skeleton totals
+  __device__ __forceinline__ float value(float f, float sqf, float Aj, float Wj, float Ej, float sumA, float sumW,
+                                         float fn) const {
+    const float mun = c.mu / fn;
+    const float inner = __fmaf_rn(0.5f, __fmaf_rn(fn, Aj, -sumA), __fmaf_rn(fn, Wj, -sumW));
+    const float d = __fmaf_rn(-mun, inner, __fmul_rn(__fmul_rn(mun, sqf), Ej));
+    float v = __fmaf_rn(d, c.dt, f);
+    if (v > 1.0f) v = 1.0f;
+    if (v <= 0.0f) v = 0.0f;
+    return v;
+  }
+};
+
 // Square root of a field value for the band term: the hardware's approximate
 // root (sqrt.approx.f32, a few ulp), the same instruction in every tier.
 __device__ __forceinline__ float root(float x) {
@@ -225,6 +264,28 @@ struct Neighbourhood {
   }
 };
 
+// The general update of layer j on the storage-free tier: A_j, W_j and E_j
+// summed over the skeleton of the neighbourhood in ascending layer order,
+// the order of the other tiers.
+template <int DT>
+__device__ float slow_general_value(const Neighbourhood<DT>& nb, const GenCoef& gc, int j, float Fj, float sumA,
+                                    float sumW, float fn, float* Aout = nullptr, float* Wout = nullptr) {
+  float Aj = 0.0f, Wj = 0.0f, Ej = 0.0f, G, F;
+  for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+    nb.sums(l, G, F);
+    if (!in_skeleton(F, G)) continue;
+    Aj = __fmaf_rn(gc.a(j, l), G, Aj);
+    Wj = __fmaf_rn(gc.w(j, l), F, Wj);
+    Ej = __fmaf_rn(gc.e(j, l), root(F), Ej);
+  }
+  if (Aout) {
+    *Aout = Aj;
+    *Wout = Wj;
+    return 0.0f;
+  }
+  return gc.value(Fj, root(Fj), Aj, Wj, Ej, sumA, sumW, fn);
+}
+
 // Register map of the fast path: layer id (-1 = empty), G and F per slot.
 struct SlotMap {
   int id[kSlots];
@@ -302,7 +363,7 @@ struct MedMap {
 // ---------------------------------------------------------------------------
 enum : int { kFast = 0, kMedium = 1, kSlow = 2 };
 
-template <int DT>
+template <int DT, bool GEN>
 __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_constant__ BatchParams P) {
   using V = Val<DT>;
   using T = typename V::T;
@@ -338,6 +399,17 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
   const FieldBuf in = J.buf[par];
   const FieldBuf out = J.buf[par ^ 1];
   const Coefs& c = J.c;
+  // general coefficient matrices: only in the GEN form, and only for a job
+  // that has them (a class-coefficient job runs the class update there too)
+  const bool general = GEN && (J.cW != nullptr || J.cA != nullptr || J.cE != nullptr);
+  GenCoef gc;
+  gc.W = J.cW;
+  gc.A = J.cA;
+  gc.E = J.cE;
+  gc.K1 = J.n_layers;
+  gc.base = J.n_layers - 1;
+  gc.c = J.c;
+  float gsumA = 0.0f, gsumW = 0.0f;        // skeleton totals of the general update (storage-free tier)
   DevStatus* st = J.st;
 
   Neighbourhood<DT> nb;
@@ -615,12 +687,41 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
         ins[s] = s < mp.cnt && in_skeleton(mp.f[s], mp.g[s]);
         if (ins[s]) add_to_sums(S, mp.id[s] == base, mp.f[s], mp.g[s], sq[s]);
       }
-      const Update U(S, c);
+      if (general) {
+        const float fn = static_cast<float>(S.nC + S.hasb);
+        float Aj[kSlots], Wj[kSlots], Ej[kSlots];
+        float sumA = 0.0f, sumW = 0.0f;
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
-        if (ins[s]) {
-          vnew[s] = U.value(mp.id[s] == base, mp.f[s], mp.g[s], sq[s], S, c);
-          tot += vnew[s];
+        for (int s = 0; s < kSlots; ++s) {
+          Aj[s] = Wj[s] = Ej[s] = 0.0f;
+          if (ins[s]) {
+#pragma unroll
+            for (int l = 0; l < kSlots; ++l) {
+              if (ins[l]) {
+                Aj[s] = __fmaf_rn(gc.a(mp.id[s], mp.id[l]), mp.g[l], Aj[s]);
+                Wj[s] = __fmaf_rn(gc.w(mp.id[s], mp.id[l]), mp.f[l], Wj[s]);
+                Ej[s] = __fmaf_rn(gc.e(mp.id[s], mp.id[l]), sq[l], Ej[s]);
+              }
+            }
+            sumA = __fadd_rn(sumA, Aj[s]);
+            sumW = __fadd_rn(sumW, Wj[s]);
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          if (ins[s]) {
+            vnew[s] = gc.value(mp.f[s], sq[s], Aj[s], Wj[s], Ej[s], sumA, sumW, fn);
+            tot += vnew[s];
+          }
+        }
+      } else {
+        const Update U(S, c);
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          if (ins[s]) {
+            vnew[s] = U.value(mp.id[s] == base, mp.f[s], mp.g[s], sq[s], S, c);
+            tot += vnew[s];
+          }
         }
       }
       if (!(tot > 0.0f)) zero_sum = true;
@@ -636,13 +737,45 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
       // ---- medium path: the same update over the shared-memory map ----------
       for (int s = 0; s < med.cnt; ++s)
         if (in_skeleton(med.f[s], med.g[s])) add_to_sums(S, med.id[s] == base, med.f[s], med.g[s], root(med.f[s]));
-      const Update U(S, c);
-      for (int s = 0; s < med.cnt; ++s) {
-        if (in_skeleton(med.f[s], med.g[s])) {
-          med.g[s] = U.value(med.id[s] == base, med.f[s], med.g[s], root(med.f[s]), S, c);
-          tot += med.g[s];
-        } else {
-          med.f[s] = -1.0f;                      // not in the skeleton
+      if (general) {
+        const float fn = static_cast<float>(S.nC + S.hasb);
+        float sumA = 0.0f, sumW = 0.0f;
+        float vt[kMed];
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int s = 0; s < med.cnt; ++s) {
+            if (!in_skeleton(med.f[s], med.g[s])) continue;
+            float Aj = 0.0f, Wj = 0.0f, Ej = 0.0f;
+            for (int l = 0; l < med.cnt; ++l) {
+              if (!in_skeleton(med.f[l], med.g[l])) continue;
+              Aj = __fmaf_rn(gc.a(med.id[s], med.id[l]), med.g[l], Aj);
+              Wj = __fmaf_rn(gc.w(med.id[s], med.id[l]), med.f[l], Wj);
+              Ej = __fmaf_rn(gc.e(med.id[s], med.id[l]), root(med.f[l]), Ej);
+            }
+            if (pass == 0) {
+              sumA = __fadd_rn(sumA, Aj);
+              sumW = __fadd_rn(sumW, Wj);
+            } else {
+              vt[s] = gc.value(med.f[s], root(med.f[s]), Aj, Wj, Ej, sumA, sumW, fn);
+            }
+          }
+        }
+        for (int s = 0; s < med.cnt; ++s) {
+          if (in_skeleton(med.f[s], med.g[s])) {
+            med.g[s] = vt[s];
+            tot += med.g[s];
+          } else {
+            med.f[s] = -1.0f;                    // not in the skeleton
+          }
+        }
+      } else {
+        const Update U(S, c);
+        for (int s = 0; s < med.cnt; ++s) {
+          if (in_skeleton(med.f[s], med.g[s])) {
+            med.g[s] = U.value(med.id[s] == base, med.f[s], med.g[s], root(med.f[s]), S, c);
+            tot += med.g[s];
+          } else {
+            med.f[s] = -1.0f;                    // not in the skeleton
+          }
         }
       }
       if (!(tot > 0.0f)) zero_sum = true;
@@ -661,15 +794,28 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
         if (in_skeleton(F, G)) add_to_sums(S, l == base, F, G, root(F));
       }
       const Update U(S, c);
+      const float fn = static_cast<float>(S.nC + S.hasb);
+      if (general) {
+        for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+          nb.sums(l, G, F);
+          if (!in_skeleton(F, G)) continue;
+          float Aj, Wj;
+          slow_general_value(nb, gc, l, F, 0.0f, 0.0f, fn, &Aj, &Wj);
+          gsumA = __fadd_rn(gsumA, Aj);
+          gsumW = __fadd_rn(gsumW, Wj);
+        }
+      }
+      auto value = [&](int l, float F, float G) {
+        return general ? slow_general_value(nb, gc, l, F, gsumA, gsumW, fn) : U.value(l == base, F, G, root(F), S, c);
+      };
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
-        if (in_skeleton(F, G)) tot += U.value(l == base, F, G, root(F), S, c);
+        if (in_skeleton(F, G)) tot += value(l, F, G);
       }
       if (!(tot > 0.0f)) zero_sum = true;
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
-        if (in_skeleton(F, G) && V::widen(V::round(__fmul_rn(U.value(l == base, F, G, root(F), S, c), 1.0f / tot))) != 0.0f)
-          ++kept;
+        if (in_skeleton(F, G) && V::widen(V::round(__fmul_rn(value(l, F, G), 1.0f / tot))) != 0.0f) ++kept;
       }
     }
     nsk = S.nC + S.hasb;
@@ -742,12 +888,14 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
       }
     } else {
       const Update U(S, c);
+      const float fn = static_cast<float>(S.nC + S.hasb);
       float G, F;
       int o = off;
       for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
         nb.sums(l, G, F);
         if (!in_skeleton(F, G)) continue;
-        const T vt = V::round(__fmul_rn(U.value(l == base, F, G, root(F), S, c), 1.0f / tot));
+        const float v = general ? slow_general_value(nb, gc, l, F, gsumA, gsumW, fn) : U.value(l == base, F, G, root(F), S, c);
+        const T vt = V::round(__fmul_rn(v, 1.0f / tot));
         if (V::widen(vt) != 0.0f) {
           put(o, l, vt);
           ++o;
@@ -803,6 +951,29 @@ __global__ void seed_scatter_kernel(const __grid_constant__ JobDesc job, int k, 
   const int v = seeds[s];
   const int tile = v / kTile;
   job.buf[0].ids[tile * job.tile_cap + (v - tile * kTile)] = static_cast<uint16_t>(s);
+}
+
+// Region seeds (Sec. 3.2, "Initialization"): the seed vertex and its
+// immediate neighbours take the seed's layer.  A vertex claimed by several
+// seeds goes to its own seed if it is one, else to the lowest seed id:
+// key = (neighbour ? 2^20 : 0) | seed, smallest key wins.
+__global__ void region_claim_kernel(const __grid_constant__ JobDesc job, int k, const int32_t* __restrict__ seeds,
+                                    unsigned* __restrict__ owner) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= k) return;
+  const int v = seeds[s];
+  atomicMin(&owner[v], static_cast<unsigned>(s));
+  for (int q = job.L_rowptr[v]; q < job.L_rowptr[v + 1]; ++q)
+    atomicMin(&owner[job.L_colval[q].x], (1u << 20) | static_cast<unsigned>(s));
+}
+
+__global__ void region_scatter_kernel(const __grid_constant__ JobDesc job, const unsigned* __restrict__ owner) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= job.n_v) return;
+  const unsigned o = owner[i];
+  if (o == ~0u) return;
+  const int tile = i / kTile;
+  job.buf[0].ids[tile * job.tile_cap + (i - tile * kTile)] = static_cast<uint16_t>(o & 0xfffffu);
 }
 
 template <int DT>
@@ -876,13 +1047,21 @@ __global__ void narrow_kernel(const float* __restrict__ src, void* __restrict__ 
 }
 
 using StepFn = void (*)(const BatchParams);
-const StepFn kStepFns[3] = {&step_kernel_impl<0>, &step_kernel_impl<1>, &step_kernel_impl<2>};
+const StepFn kStepFns[3][2] = {{&step_kernel_impl<0, false>, &step_kernel_impl<0, true>},
+                                {&step_kernel_impl<1, false>, &step_kernel_impl<1, true>},
+                                {&step_kernel_impl<2, false>, &step_kernel_impl<2, true>}};
 
 }  // namespace
 
 int step_slots() { return kSlots; }
 
-const void* step_kernel(int dtype) { return reinterpret_cast<const void*>(kStepFns[dtype]); }
+const void* step_kernel(int dtype, bool general) { return reinterpret_cast<const void*>(kStepFns[dtype][general]); }
+
+bool needs_general(const BatchParams& p) {
+  for (int j = 0; j < p.n_jobs; ++j)
+    if (p.job[j].cW || p.job[j].cA || p.job[j].cE) return true;
+  return false;
+}
 
 cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
@@ -895,7 +1074,7 @@ cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kStepFns[dtype], p);
+  return cudaLaunchKernelEx(&cfg, kStepFns[dtype][needs_general(p)], p);
 }
 
 #define LF_DISPATCH(dtype, KERNEL, GRID, BLOCK, STREAM, ...)                       \
@@ -909,6 +1088,18 @@ cudaError_t launch_seed(const JobDesc& job, int k, const int32_t* d_seeds, int d
   const int blocks = (job.n_v + 255) / 256;
   LF_DISPATCH(dtype, seed_fill_kernel, blocks, 256, s, job, k);
   seed_scatter_kernel<<<(k + 255) / 256, 256, 0, s>>>(job, k, d_seeds);
+  LF_DISPATCH(dtype, build_head_kernel, blocks, 256, s, job.buf[0], job.n_v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_regions(const JobDesc& job, int k, const int32_t* d_seeds, unsigned* d_owner, int dtype,
+                                cudaStream_t s) {
+  const int blocks = (job.n_v + 255) / 256;
+  cudaError_t e = cudaMemsetAsync(d_owner, 0xff, sizeof(unsigned) * static_cast<size_t>(job.n_v), s);
+  if (e != cudaSuccess) return e;
+  LF_DISPATCH(dtype, seed_fill_kernel, blocks, 256, s, job, k);
+  region_claim_kernel<<<(k + 255) / 256, 256, 0, s>>>(job, k, d_seeds, d_owner);
+  region_scatter_kernel<<<blocks, 256, 0, s>>>(job, d_owner);
   LF_DISPATCH(dtype, build_head_kernel, blocks, 256, s, job.buf[0], job.n_v);
   return cudaGetLastError();
 }

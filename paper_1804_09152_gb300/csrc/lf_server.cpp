@@ -74,6 +74,7 @@ struct lf_server_s {
   std::condition_variable cv_done;   // waiters: a job finished
   std::deque<JobPtr> queue;
   std::vector<JobPtr> running;       // admitted (the scheduler owns their meshes)
+  int64_t admitting = 0;             // taken from the queue, being created on the device
   std::unordered_map<int64_t, JobPtr> jobs;
   int64_t next_id = 1;
   bool stop = false;
@@ -141,6 +142,7 @@ void scheduler(lf_server_s* s) {
         used += j->bytes_est;
         s->queue.pop_front();
         admit.push_back(j);
+        ++s->admitting;
       }
     }
     // create and seed the admitted jobs (outside the lock: the upload is long)
@@ -160,6 +162,7 @@ void scheduler(lf_server_s* s) {
       j->admit_ns = now_ns();
       j->state = LF_JOB_RUNNING;
       s->running.push_back(j);
+      --s->admitting;
       if (r != LF_OK) {
         j->status = r;                 // retired below, before any step
       } else {
@@ -419,7 +422,7 @@ lf_status lf_server_dual_mesh(lf_server s, int64_t job_id, int32_t* tris, int64_
 lf_status lf_server_drain(lf_server s, double timeout_s) {
   if (!s) return server_fail(LF_ERR_INVALID, "null server");
   std::unique_lock<std::mutex> lk(s->mu);
-  auto idle = [&] { return s->queue.empty() && s->running.empty(); };
+  auto idle = [&] { return s->queue.empty() && s->running.empty() && s->admitting == 0; };
   if (timeout_s > 0.0) s->cv_done.wait_for(lk, std::chrono::duration<double>(std::min(timeout_s, 1e7)), idle);
   return idle() ? LF_OK : LF_ERR_TIMEOUT;
 }
@@ -429,7 +432,7 @@ lf_status lf_server_stats(lf_server s, lf_server_stats_t* out) {
   std::lock_guard<std::mutex> lk(s->mu);
   *out = s->st;
   out->queued = static_cast<int64_t>(s->queue.size());
-  out->running = static_cast<int64_t>(s->running.size());
+  out->running = static_cast<int64_t>(s->running.size()) + s->admitting;
   out->bytes_in_use = reserved_bytes(s);
   return LF_OK;
 }

@@ -111,3 +111,11 @@ def test_lloyd_needs_geometry_and_seeds(lf, oracle_mod):
         with pytest.raises(lf.LFError) as ei:
             lf.lf_lloyd(mesh.h, -1, 0, 5)
         assert ei.value.status == lf.LF_ERR_INVALID
+
+
+def test_symmetric_seeds_are_stationary_on_the_gpu(lf):
+    m = synth.icosphere(4)
+    with lf.Mesh(m.V, m.F) as mesh:
+        mesh.seed(np.arange(12, dtype=np.int32))
+        mesh.step(150)
+        assert np.array_equal(mesh.lloyd(1, 0), np.arange(12))

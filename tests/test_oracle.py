@@ -329,6 +329,58 @@ def test_general_matrices_three_layers_by_hand(oracle_mod):
         assert abs(got[l] - ref[l]) < 1e-14
 
 
+def test_general_a_matrix_and_interest_layer_by_hand(oracle_mod):
+    """The a_jl term and a layer entering through G > 0, on a two-vertex path.
+
+    With L = [[-1, 1], [1, -1]], vertex 0 holds {0: .6, 1: .4} and vertex 1
+    {0: .2, 2: .8}: at vertex 0, G = F_1 - F_0 = (-.4, -.4, .8), so layer 2
+    joins the skeleton with F = 0.  With W = E = 0 the update of layer j is
+    d_j = -(mu/n) sum_k (1/2) (A G)_j - (A G)_k over the skeleton, written
+    here with matrix products over the skeleton only.
+    """
+    rng = np.random.default_rng(4)
+    A = rng.random((3, 3))
+    L = oracle_mod.operator_from_dense(np.array([[-1.0, 1.0], [1.0, -1.0]]))
+    F = make_field(oracle_mod, [{0: .6, 1: .4}, {0: .2, 2: .8}], 3)
+    dt, mu = 0.5, 1.0
+    out, _ = oracle_mod.step(L, F, dict(dt=dt, mu=mu), W=np.zeros((3, 3)), A=A, E=np.zeros((3, 3)))
+    Fv = np.array([.6, .4, 0.0])
+    G = np.array([-.4, -.4, .8])
+    AG = A @ G                                    # all three layers are in the skeleton
+    n = 3
+    d = -(mu / n) * 0.5 * (n * AG - AG.sum())
+    ref = normalise({j: clamp(Fv[j] + dt * d[j]) for j in range(3)})
+    got = row_dict(out, 0)
+    assert set(got) == {j for j in ref if ref[j] > 0}
+    for l in got:
+        assert abs(got[l] - ref[l]) < 1e-14
+
+
+def test_class_rule_as_matrices_equals_the_class_step(oracle_mod):
+    """The class coefficients written out as dense matrices give the class step."""
+    m = synth.planar_grid(14, seed=3)
+    k = 6
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    F = oracle_mod.seed(m.n_v, synth.sample_seeds(m.n_v, k, 2))
+    for _ in range(15):
+        F, _ = oracle_mod.step(L, F)
+    n = k + 1
+    p = oracle_mod.DEFAULT_PARAMS
+    cell = np.arange(n) < k
+    both = np.outer(cell, cell)
+    W = np.where(both, p["w_cc"], p["w_cb"])
+    A = np.where(both, p["a_cc"], p["a_cb"])
+    E = np.where(both, p["e_cc"], 0.0)
+    E[cell, k] = p["e_cb"]
+    E[k, cell] = p["e_bc"]
+    for M in (W, A, E):
+        np.fill_diagonal(M, 0.0)
+    a, ska = oracle_mod.step(L, F)
+    b, skb = oracle_mod.step(L, F, W=W, A=A, E=E)
+    assert ska == skb and np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.ids, b.ids)
+    assert np.abs(a.vals - b.vals).max() < 1e-15
+
+
 def test_single_layer_is_fixed_point(oracle_mod):
     m = synth.planar_grid(12)
     L = oracle_mod.cotan_laplacian(m.V, m.F)

@@ -138,3 +138,20 @@ def test_lloyd_rounds_balance_the_cells(oracle_mod):
         assert len(set(seeds.tolist())) == k
         F, s1 = sizes(seeds)
     assert s1.std() / s1.mean() < 0.6 * (s0.std() / s0.mean())
+
+
+def test_symmetric_seeds_are_stationary(oracle_mod):
+    # the 12 icosahedron vertices as seeds on the subdivided icosahedron: each
+    # cell is symmetric about its seed's axis, so its centre of mass and normal
+    # lie on that axis and the back-projection returns the seed itself
+    m = synth.icosphere(3)
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    seeds = np.arange(12)
+    F = oracle_mod.seed(m.n_v, seeds)
+    for _ in range(60):
+        F, _ = oracle_mod.step(L, F)
+    frames = tz.cell_frames(m.V, m.F, F, 12)
+    for c, (P, d, ts) in enumerate(frames):
+        axis = m.V[c] / np.linalg.norm(m.V[c])
+        assert abs(abs(d @ axis) - 1.0) < 1e-3          # normal along the seed axis
+    assert np.array_equal(tz.lloyd_seeds(m.V, m.F, F, seeds), seeds)
