@@ -46,7 +46,7 @@ WORKLOADS = {
 
 # DRAM bytes of one step-kernel launch from an ncu capture of the grid512
 # workload, valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"kernel_sha": "0ea4d3d1fff8227e", "bytes_per_launch": 17856597}
+NCU_TRAFFIC = {"kernel_sha": "6932ba2487f95031", "bytes_per_launch": 17856939}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -405,6 +405,25 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def cell_area_stats(m, labels, k):
+    """Areas of the cells of a labelling (a vertex carries a third of the area
+    of each face around it): coefficient of variation and a histogram of
+    area / mean area."""
+    P = m.V[m.F]
+    fa = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    va = np.zeros(m.n_v)
+    for c in range(3):
+        np.add.at(va, m.F[:, c], fa / 3.0)
+    cov = labels >= 0
+    area = np.bincount(labels[cov], weights=va[cov], minlength=k)
+    rel = area / area.mean()
+    edges = [0.0, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0, np.inf]
+    hist, _ = np.histogram(rel, bins=edges)
+    return {"cv": float(area.std() / area.mean()), "min_rel": float(rel.min()), "max_rel": float(rel.max()),
+            "hist_edges": [e if np.isfinite(e) else "inf" for e in edges], "hist": hist.tolist(),
+            "empty_cells": int((area == 0).sum()), "base_vertices": int((~cov).sum())}
+
+
 def run_lloyd(args):
     """C2 with the paper's full pipeline (Sec. 5): 2000 steps, then Lloyd-like
     rounds (seed update + 2000 steps each), then the dual mesh (Sec. 5.2)."""
@@ -455,6 +474,13 @@ def run_lloyd(args):
                 flush.zero_()
                 torch.cuda.synchronize()
                 res.append(pipeline())
+        # cell areas before and after the rounds (untimed run of the same pipeline)
+        mesh.seed(seeds)
+        mesh.step(T)
+        areas = [cell_area_stats(m, mesh.labels(), wl["k"])]
+        for _ in range(R):
+            mesh.lloyd(1, T)
+        areas.append(cell_area_stats(m, mesh.labels(), wl["k"]))
         mesh.close()
     total_ms = sum(r[0] for r in res)
     units = sum(r[3] for r in res)
@@ -468,6 +494,43 @@ def run_lloyd(args):
         "lloyd_update_ms": statistics.mean(r[1] for r in res),
         "dual_extraction_ms": statistics.mean(r[2] for r in res),
         "dual_triangles": res[-1][4],
+        "cell_areas": {"before_lloyd": areas[0], f"after_{R}_rounds": areas[1]},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_dt_sweep(args):
+    """The Δt study of Sec. 6 on synthetic irregular meshes: the same seeds at
+    Δt = 0.1, 1, 5 and 10 for the same simulated time (300 units), labels
+    read every unit of simulated time; agreement of the final labels with
+    those at Δt = 0.1 and the step count after which no label changes."""
+    import torch
+    import paper_1804_09152_gb300 as pkg
+    pkg.build()
+    from paper_1804_09152_gb300 import study
+
+    meshes = {"torus256": lambda: synth.noisy_torus(256), "ico6": lambda: synth.icosphere(6),
+              "grid256": lambda: synth.planar_grid(256, jitter=0.2, seed=2)}
+    dts = (0.1, 1.0, 5.0, 10.0)
+    k, horizon = 256, 300.0
+    res, units, total_ms = {}, 0, 0.0
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for name, fac in meshes.items():
+            m = fac()
+            r = study.dt_sweep(m.V, m.F, synth.sample_seeds(m.n_v, k, 11), dts, horizon=horizon)
+            res[name] = {str(dt): {key: v for key, v in x.items() if key != "labels"} for dt, x in r.items()}
+            res[name]["n_v"] = m.n_v
+            units += sum(x["skeleton_total"] for x in r.values())
+            total_ms += sum(x["ms"] for x in r.values())
+    line = {
+        "metric": METRIC, "value": units / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": total_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "dt_sweep", "desc": f"noisy torus 256^2, icosphere level 6, jittered grid 256^2; "
+                   f"{k} seeds (stream 11); dt in {list(dts)}, {horizon:g} units of simulated time each, "
+                   "labels read every unit", "timing": "host wall clock of each run, label reads included"},
+        "study": res,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -554,7 +617,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch64", "serve", "grid512_lloyd"],
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch64", "serve", "grid512_lloyd", "dt_sweep"],
                     default="grid512")
     ap.add_argument("--lloyd-rounds", type=int, default=10)
     ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default=None,
@@ -570,6 +633,8 @@ def main():
         return run_serve(args)
     if args.workload == "grid512_lloyd":
         return run_lloyd(args)
+    if args.workload == "dt_sweep":
+        return run_dt_sweep(args)
     wl = dict(WORKLOADS[args.workload])
     if args.dtype:
         wl["dtype"] = args.dtype
