@@ -268,7 +268,7 @@ def run_ours(args, wl):
             torch.cuda.synchronize()
             e2e_t += time.perf_counter() - t0
             e2e_units += s["skeleton_total"]
-    h2d = 4 * (m.n_v + 1) + 8 * st["operator_nnz"] + 4 * wl["k"]
+    h2d = 24 * m.n_v + 12 * m.n_f + 4 * wl["k"]          # vertices, faces, seeds (the operator is built on the device)
     d2h = 4 * m.n_v
 
     line = {

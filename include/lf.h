@@ -119,8 +119,10 @@ void lf_default_params(lf_params* p);
  * Builds the static operator of a triangle mesh: the cotangent Laplacian
  * (precomputed once, Sec. 3.2), L_ij = (cot alpha_ij + cot beta_ij) / 2 over
  * the angles opposite edge ij, L_ii = -sum_j L_ij, no mass matrix; every edge
- * is kept even when its weight is 0.  Computed in FP64 on the host, stored on
- * the device as FP32 CSR without the diagonal.
+ * is kept even when its weight is 0.  The mesh is copied to the device once
+ * (it stays there for lf_lloyd and lf_extract_dual) and the operator is built
+ * there in FP64, summed over the faces in face order, and stored as FP32 CSR
+ * without the diagonal (lf_get_operator reads it back).
  *   V: n_v x 3 doubles, row-major.  F: n_f x 3 int32 vertex ids, 0-based.
  *   params: copied; may be NULL for the defaults.
  * Errors: LF_ERR_INVALID for n_v < 3, n_v >= 2^31, n_f < 1, an id out of
@@ -227,6 +229,18 @@ lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters);
  * Errors: LF_ERR_STATE before lf_seed.
  */
 lf_status lf_labels(lf_mesh m, int32_t* labels, float* maxval);
+
+/*
+ * Copies the mesh's operator to the host as it is stored: the off-diagonal
+ * entries L_ij (i != j) as CSR, rowptr (n_v + 1 int64), col (int32,
+ * increasing in each row), val (float); L_ii = -sum_j L_ij is implied.  For
+ * lf_create_mesh that is the cotangent Laplacian of Sec. 3.2 (half the sum
+ * of the cotangents opposite each edge), built on the device in FP64 and
+ * rounded to FP32 once.  With col or val NULL, or cap below the entry count,
+ * only *nnz and rowptr (if non-NULL) are written: a size query.
+ * Errors: LF_ERR_INVALID for a NULL nnz.
+ */
+lf_status lf_get_operator(lf_mesh m, int64_t* rowptr, int32_t* col, float* val, int64_t cap, int64_t* nnz);
 
 /*
  * Copies the current field to the host as CSR: rowptr (n_v + 1 int64),

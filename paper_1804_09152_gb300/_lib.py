@@ -102,6 +102,8 @@ _lib.lf_step.argtypes = [_P, _i32]
 _lib.lf_step.restype = ctypes.c_int
 _lib.lf_labels.argtypes = [_P, _P, _P]
 _lib.lf_labels.restype = ctypes.c_int
+_lib.lf_get_operator.argtypes = [_P, _P, _P, _P, _i64, ctypes.POINTER(_i64)]
+_lib.lf_get_operator.restype = ctypes.c_int
 _lib.lf_get_field.argtypes = [_P, _P, _P, _P, _i64, ctypes.POINTER(_i64)]
 _lib.lf_get_field.restype = ctypes.c_int
 _lib.lf_set_field.argtypes = [_P, _P, _P, _P, _i64, _i32]
@@ -143,7 +145,7 @@ _lib.lf_server_destroy.restype = None
 
 EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_seed_regions",
             "lf_set_coefficients", "lf_step", "lf_labels",
-            "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
+            "lf_get_operator", "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
             "lf_step_noalloc", "lf_step_batch", "lf_lloyd", "lf_extract_dual", "lf_server_default_params", "lf_server_create",
             "lf_server_submit", "lf_server_wait", "lf_server_dual_mesh", "lf_server_drain", "lf_server_stats", "lf_server_destroy"]
 
@@ -298,6 +300,17 @@ def lf_get_field(mesh, n_v):
     return rp, lay[:nnz.value].copy(), val[:nnz.value].copy()
 
 
+def lf_get_operator(mesh, n_v):
+    """Returns the stored off-diagonal operator (rowptr int64, col int32, val float32)."""
+    nnz = _i64()
+    rp = np.empty(n_v + 1, np.int64)
+    _check(_lib.lf_get_operator(mesh, _ptr(rp), None, None, 0, ctypes.byref(nnz)), mesh)
+    col = np.empty(max(nnz.value, 1), np.int32)
+    val = np.empty(max(nnz.value, 1), np.float32)
+    _check(_lib.lf_get_operator(mesh, _ptr(rp), _ptr(col), _ptr(val), col.size, ctypes.byref(nnz)), mesh)
+    return rp, col[:nnz.value].copy(), val[:nnz.value].copy()
+
+
 def lf_set_field(mesh, rowptr, layer, val, n_layers):
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     layer = np.ascontiguousarray(layer, dtype=np.int32)
@@ -381,6 +394,9 @@ class Mesh:
 
     def get_field(self):
         return lf_get_field(self.h, self.n_v)
+
+    def get_operator(self):
+        return lf_get_operator(self.h, self.n_v)
 
     def set_field(self, rowptr, layer, val, n_layers):
         lf_set_field(self.h, rowptr, layer, val, n_layers)

@@ -421,22 +421,25 @@ lf_status check_usable(lf_mesh m) {
 }
 
 // Common tail of both create paths: off-diagonal FP64 CSR -> device.
-lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int64_t>& rp,
-                        const std::vector<int32_t>& col, const std::vector<double>& val,
-                        const lf_params& prm, lf_mesh* out) {
+// A mesh handle without operator or field: stream, parameters, tile count.
+lf_mesh new_mesh(const lf_device* dev, int64_t n_v, const lf_params& prm) {
   lf_mesh m = new (std::nothrow) lf_mesh_s();
-  if (!m) return fail(nullptr, LF_ERR_OOM, "host allocation");
+  if (!m) return nullptr;
   if (dev) m->dev = *dev;
   m->stream = static_cast<cudaStream_t>(m->dev.cuda_stream);
   m->params = prm;
   m->n_v = n_v;
   m->dtype = prm.field_dtype;
   m->num_tiles = static_cast<int>((n_v + lf::kTile - 1) / lf::kTile);
+  return m;
+}
+
+// Off-diagonal FP64 CSR from the host -> the device operator (FP32 values).
+lf_status upload_operator(lf_mesh m, const std::vector<int64_t>& rp, const std::vector<int32_t>& col,
+                          const std::vector<double>& val) {
+  const int64_t n_v = m->n_v;
   const int64_t nnz = static_cast<int64_t>(col.size());
-  if (nnz >= kMaxCap) {
-    delete m;
-    return fail(nullptr, LF_ERR_CAPACITY, "operator exceeds 2^31 entries");
-  }
+  if (nnz >= kMaxCap) return fail(m, LF_ERR_CAPACITY, "operator exceeds 2^31 entries");
   m->L_nnz = nnz;
   std::vector<int32_t> rp32(static_cast<size_t>(n_v) + 1);
   for (int64_t i = 0; i <= n_v; ++i) rp32[static_cast<size_t>(i)] = static_cast<int32_t>(rp[static_cast<size_t>(i)]);
@@ -449,28 +452,79 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
   }
   m->d_Lrp = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * (n_v + 1)));
   m->d_Lcv = static_cast<int2*>(m->dalloc(sizeof(int2) * std::max<int64_t>(nnz, 1)));
+  if (!m->d_Lrp || !m->d_Lcv) return fail(m, LF_ERR_OOM, "device allocation");
+  LF_CUDA(m, cudaMemcpyAsync(m->d_Lrp, rp32.data(), sizeof(int32_t) * (n_v + 1), cudaMemcpyHostToDevice, m->stream));
+  LF_CUDA(m, cudaMemcpyAsync(m->d_Lcv, cv.data(), sizeof(int2) * std::max<int64_t>(nnz, 1), cudaMemcpyHostToDevice,
+                             m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));   // the host vectors die on return
+  return LF_OK;
+}
+
+// The cotangent operator built on the device from the mesh's own geometry
+// (d_V, d_tri): the same bits as cotan_rows + upload_operator.
+lf_status build_operator_device(lf_mesh m) {
+  const int64_t n_v = m->n_v, n_f = m->n_f;
+  if (6 * n_f >= kMaxCap) return fail(m, LF_ERR_CAPACITY, "operator exceeds 2^31 entries");
+  const int64_t nb = std::max(lf::cotan_scan_blocks(n_v), int64_t{1});
+  auto* hc = static_cast<double*>(m->dalloc(sizeof(double) * 3 * static_cast<size_t>(n_f)));
+  auto* inc = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * 3 * static_cast<size_t>(n_f)));
+  auto* cnt = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * static_cast<size_t>(n_v)));
+  auto* inc_start = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * static_cast<size_t>(n_v + 1)));
+  auto* bsum = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * static_cast<size_t>(nb)));
+  auto* bad = static_cast<unsigned long long*>(m->dalloc(sizeof(unsigned long long)));
+  m->d_Lrp = static_cast<int32_t*>(m->dalloc(sizeof(int32_t) * static_cast<size_t>(n_v + 1)));
+  auto release = [&]() {
+    for (void* p : {static_cast<void*>(hc), static_cast<void*>(inc), static_cast<void*>(cnt),
+                    static_cast<void*>(inc_start), static_cast<void*>(bsum), static_cast<void*>(bad)})
+      m->dfree(p);
+  };
+  if (!hc || !inc || !cnt || !inc_start || !bsum || !bad || !m->d_Lrp) {
+    release();
+    return fail(m, LF_ERR_OOM, "operator build scratch");
+  }
+  cudaStream_t st = m->stream;
+  int32_t total = 0;
+  unsigned long long first_bad = 0;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n_v, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = lf::launch_cotan_corners(m->d_V, m->d_tri, n_f, hc, cnt, bad, st);
+  if (e == cudaSuccess) e = lf::launch_exclusive_scan(cnt, inc_start, n_v, bsum, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n_v, st);
+  if (e == cudaSuccess) e = lf::launch_cotan_incidence(m->d_tri, n_f, inc_start, cnt, inc, st);
+  if (e == cudaSuccess) e = lf::launch_cotan_rows(m->d_tri, hc, n_v, inc_start, inc, 0, cnt, nullptr, nullptr, st);
+  if (e == cudaSuccess) e = lf::launch_exclusive_scan(cnt, m->d_Lrp, n_v, bsum, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, m->d_Lrp + n_v, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&first_bad, bad, sizeof(first_bad), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && first_bad == ~0ull) {
+    m->L_nnz = total;
+    m->d_Lcv = static_cast<int2*>(m->dalloc(sizeof(int2) * static_cast<size_t>(std::max<int64_t>(total, 1))));
+    if (!m->d_Lcv) {
+      release();
+      return fail(m, LF_ERR_OOM, "device allocation");
+    }
+    e = lf::launch_cotan_rows(m->d_tri, hc, n_v, inc_start, inc, 1, nullptr, m->d_Lrp, m->d_Lcv, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  release();
+  if (e != cudaSuccess) return cuda_fail(m, e, "building the operator");
+  if (first_bad != ~0ull) return fail(m, LF_ERR_INVALID, "face " + std::to_string(first_bad) + " has zero area");
+  return LF_OK;
+}
+
+// Common tail of both create paths: status word, row arrays, job descriptor,
+// tile segments.
+lf_status finish_setup(lf_mesh m, const lf_params& prm) {
+  const int64_t n_v = m->n_v;
   m->d_st = static_cast<lf::DevStatus*>(m->dalloc(sizeof(lf::DevStatus)));
   for (int b = 0; b < 2; ++b) {
     m->buf[b].rows = static_cast<int2*>(m->dalloc(sizeof(int2) * n_v));
     m->buf[b].head = static_cast<int4*>(m->dalloc(sizeof(int4) * n_v));
   }
-  if (!m->d_Lrp || !m->d_Lcv || !m->d_st || !m->buf[0].rows || !m->buf[1].rows || !m->buf[0].head ||
-      !m->buf[1].head) {
-    delete m;
-    return fail(nullptr, LF_ERR_OOM, "device allocation");
-  }
-  cudaError_t e = cudaMemcpyAsync(m->d_Lrp, rp32.data(), sizeof(int32_t) * (n_v + 1), cudaMemcpyHostToDevice,
-                                  m->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(m->d_Lcv, cv.data(), sizeof(int2) * std::max<int64_t>(nnz, 1), cudaMemcpyHostToDevice,
-                        m->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_st, 0, sizeof(lf::DevStatus), m->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    delete m;
-    return fail(nullptr, LF_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
-  }
+  if (!m->d_st || !m->buf[0].rows || !m->buf[1].rows || !m->buf[0].head || !m->buf[1].head)
+    return fail(m, LF_ERR_OOM, "device allocation");
+  LF_CUDA(m, cudaMemsetAsync(m->d_st, 0, sizeof(lf::DevStatus), m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
   lf::JobDesc& j = m->h_job;
   j.n_v = static_cast<int32_t>(n_v);
   j.n_layers = 0;
@@ -488,6 +542,11 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
                                                : 3 * lf::kTile;
   lf_status s = set_tile_cap(m, cap, false);
   if (s == LF_OK) s = upload_job(m);
+  return s;
+}
+
+// Hands a finished mesh out, or deletes a failed one keeping its message.
+lf_status hand_out(lf_mesh m, lf_status s, lf_mesh* out) {
   if (s != LF_OK) {
     g_create_error = m->err;
     delete m;
@@ -495,6 +554,17 @@ lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int
   }
   *out = m;
   return LF_OK;
+}
+
+// The host-CSR create path (lf_create_mesh_csr, the server).
+lf_status finish_create(const lf_device* dev, int64_t n_v, const std::vector<int64_t>& rp,
+                        const std::vector<int32_t>& col, const std::vector<double>& val,
+                        const lf_params& prm, lf_mesh* out) {
+  lf_mesh m = new_mesh(dev, n_v, prm);
+  if (!m) return fail(nullptr, LF_ERR_OOM, "host allocation");
+  lf_status s = upload_operator(m, rp, col, val);
+  if (s == LF_OK) s = finish_setup(m, prm);
+  return hand_out(m, s, out);
 }
 
 }  // namespace
@@ -511,19 +581,53 @@ bool mesh_ok(int64_t n_v, const double* V, int64_t n_f, const int32_t* F, std::s
   if (!V || !F) { why = "null argument"; return false; }
   if (n_v < 3 || n_v >= kMaxCap) { why = "n_v out of range"; return false; }
   if (n_f < 1) { why = "n_f must be >= 1"; return false; }
-  for (int64_t f = 0; f < n_f; ++f) {
+  std::atomic<int64_t> bad_v{n_v};
+  parallel_for(n_v, 1 << 16, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      if (!std::isfinite(V[3 * i]) || !std::isfinite(V[3 * i + 1]) || !std::isfinite(V[3 * i + 2])) {
+        int64_t cur = bad_v.load();
+        while (i < cur && !bad_v.compare_exchange_weak(cur, i)) {
+        }
+        break;
+      }
+  });
+  if (bad_v.load() < n_v) { why = "non-finite vertex coordinate"; return false; }
+  // per face: ids in range, no repeated id, and a nonzero cross product at
+  // the first corner (the first failing face is reported)
+  std::atomic<int64_t> bad_f{n_f};
+  parallel_for(n_f, 1 << 15, [&](int64_t lo, int64_t hi) {
+    for (int64_t f = lo; f < hi && f < bad_f.load(); ++f) {
+      const int32_t a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+      bool bad = false;
+      if (a < 0 || b < 0 || c < 0 || a >= n_v || b >= n_v || c >= n_v || a == b || b == c || a == c) {
+        bad = true;
+      } else {
+        const double* P = V + 3 * static_cast<int64_t>(a);
+        const double* Q = V + 3 * static_cast<int64_t>(b);
+        const double* S = V + 3 * static_cast<int64_t>(c);
+        const double ux = Q[0] - P[0], uy = Q[1] - P[1], uz = Q[2] - P[2];
+        const double wx = S[0] - P[0], wy = S[1] - P[1], wz = S[2] - P[2];
+        const double cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+        bad = cx == 0.0 && cy == 0.0 && cz == 0.0;
+      }
+      if (!bad) continue;
+      int64_t cur = bad_f.load();
+      while (f < cur && !bad_f.compare_exchange_weak(cur, f)) {
+      }
+      break;
+    }
+  });
+  const int64_t f = bad_f.load();
+  if (f < n_f) {
     const int32_t a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
-    if (a < 0 || b < 0 || c < 0 || a >= n_v || b >= n_v || c >= n_v) {
+    if (a < 0 || b < 0 || c < 0 || a >= n_v || b >= n_v || c >= n_v)
       why = "face " + std::to_string(f) + " has a vertex out of range";
-      return false;
-    }
-    if (a == b || b == c || a == c) {
+    else if (a == b || b == c || a == c)
       why = "face " + std::to_string(f) + " repeats a vertex";
-      return false;
-    }
+    else
+      why = "face " + std::to_string(f) + " has zero area";
+    return false;
   }
-  for (int64_t i = 0; i < 3 * n_v; ++i)
-    if (!std::isfinite(V[i])) { why = "non-finite vertex coordinate"; return false; }
   return true;
 }
 
@@ -609,24 +713,14 @@ lf_status lf_create_mesh(const lf_device* dev, const double* V, int64_t n_v, con
   std::string why;
   if (!params_ok(prm, why)) return fail(nullptr, LF_ERR_INVALID, why);
   if (!lf::mesh_ok(n_v, V, n_f, F, why)) return fail(nullptr, LF_ERR_INVALID, why);
-  std::vector<int64_t> rp;
-  std::vector<int32_t> col;
-  std::vector<double> val;
-  try {
-    if (!cotan_rows(n_v, V, n_f, F, rp, col, val, why)) return fail(nullptr, LF_ERR_INVALID, why);
-  } catch (const std::bad_alloc&) {
-    return fail(nullptr, LF_ERR_OOM, "host allocation");
-  }
-  lf_status s = finish_create(dev, n_v, rp, col, val, prm, out);
-  if (s != LF_OK) return s;
-  // the mesh itself stays on the device for the Lloyd-like update (Sec. 5)
-  s = lf::attach_geometry(*out, V, n_v, F, n_f);
-  if (s != LF_OK) {
-    g_create_error = (*out)->err;
-    delete *out;
-    *out = nullptr;
-  }
-  return s;
+  // the mesh goes to the device once: the operator is built there from it,
+  // and it stays for the Lloyd-like update (Sec. 5) and the dual mesh
+  lf_mesh m = new_mesh(dev, n_v, prm);
+  if (!m) return fail(nullptr, LF_ERR_OOM, "host allocation");
+  lf_status s = lf::attach_geometry(m, V, n_v, F, n_f);
+  if (s == LF_OK) s = build_operator_device(m);
+  if (s == LF_OK) s = finish_setup(m, prm);
+  return hand_out(m, s, out);
 }
 
 lf_status lf_create_mesh_csr(const lf_device* dev, int64_t n_v, const int64_t* rowptr, const int32_t* col,
@@ -958,6 +1052,29 @@ lf_status lf_labels(lf_mesh m, int32_t* labels, float* maxval) {
 
 // The current field in plain CSR on the host: the tile segments are copied
 // whole and gathered row by row.
+lf_status lf_get_operator(lf_mesh m, int64_t* rowptr, int32_t* col, float* val, int64_t cap, int64_t* nnz) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (!nnz) return fail(m, LF_ERR_INVALID, "nnz must not be NULL");
+  *nnz = m->L_nnz;
+  if (rowptr) {
+    std::vector<int32_t> rp(static_cast<size_t>(m->n_v) + 1);
+    LF_CUDA(m, cudaMemcpyAsync(rp.data(), m->d_Lrp, sizeof(int32_t) * (m->n_v + 1), cudaMemcpyDeviceToHost,
+                               m->stream));
+    LF_CUDA(m, cudaStreamSynchronize(m->stream));
+    for (int64_t i = 0; i <= m->n_v; ++i) rowptr[i] = rp[static_cast<size_t>(i)];
+  }
+  if (!col || !val || cap < m->L_nnz || m->L_nnz == 0) return LF_OK;
+  std::vector<int2> cv(static_cast<size_t>(m->L_nnz));
+  LF_CUDA(m, cudaMemcpyAsync(cv.data(), m->d_Lcv, sizeof(int2) * m->L_nnz, cudaMemcpyDeviceToHost, m->stream));
+  LF_CUDA(m, cudaStreamSynchronize(m->stream));
+  for (int64_t q = 0; q < m->L_nnz; ++q) {
+    col[q] = cv[static_cast<size_t>(q)].x;
+    std::memcpy(&val[q], &cv[static_cast<size_t>(q)].y, 4);
+  }
+  return LF_OK;
+}
+
 lf_status lf_get_field(lf_mesh m, int64_t* rowptr, int32_t* layer, float* val, int64_t cap, int64_t* nnz) {
   lf_status s = check_usable(m);
   if (s != LF_OK) return s;

@@ -108,6 +108,24 @@ cudaError_t launch_labels(const JobDesc& job, int buf, int dtype, int32_t* d_lab
                           cudaStream_t s);
 // Region seeds: each seed vertex and its neighbours in L take the seed's
 // layer (own seed first, else the lowest seed id); d_owner is n_v scratch.
+// Device build of the cotangent operator (lf_cotan.cu).
+int64_t cotan_scan_blocks(int64_t n);   // block totals an exclusive scan of n elements needs
+// out[0..n] = exclusive prefix sums of in[0..n-1], out[n] = total; block_sum
+// holds cotan_scan_blocks(n) entries (at least one).
+cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sum, cudaStream_t s);
+// Per face: hc[3f + c] = half cotangent of corner c, inc_cnt[v] += 1 per
+// corner at v, bad_face = min face index of zero area (left as is if none).
+cudaError_t launch_cotan_corners(const double* V, const int32_t* tri, int64_t n_f, double* hc, int32_t* inc_cnt,
+                                 unsigned long long* bad_face, cudaStream_t s);
+// Per face: inc[inc_start[v] + k] = f for each corner v (fill: zeroed counters).
+cudaError_t launch_cotan_incidence(const int32_t* tri, int64_t n_f, const int32_t* inc_start, int32_t* fill,
+                                   int32_t* inc, cudaStream_t s);
+// Per vertex: pass 0 sorts its face list and writes its neighbour count to
+// cnt; pass 1 writes (column, FP32 bits) at rowptr[i] in column order.
+cudaError_t launch_cotan_rows(const int32_t* tri, const double* hc, int64_t n_v, const int32_t* inc_start,
+                              int32_t* inc, int pass, int32_t* cnt, const int32_t* rowptr, int2* colval,
+                              cudaStream_t s);
+
 cudaError_t launch_seed_regions(const JobDesc& job, int k, const int32_t* d_seeds, unsigned* d_owner, int dtype,
                                 cudaStream_t s);
 // head[] of a field buffer from its rows, ids and vals.

@@ -14,10 +14,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblf.so")
-SOURCES = ["lf_kernels.cu", "lf_lloyd.cu", "lf_dual.cu", "lf_host.cpp", "lf_noalloc.cu", "lf_server.cpp"]
+SOURCES = ["lf_kernels.cu", "lf_lloyd.cu", "lf_dual.cu", "lf_cotan.cu", "lf_host.cpp", "lf_noalloc.cu",
+           "lf_server.cpp"]
 HEADERS = [os.path.join(CSRC, "lf_internal.h"), os.path.join(ROOT, "include", "lf.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-Wall,-pthread", "-I", os.path.join(ROOT, "include")]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-Wall,-pthread,-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
 
 
 def _nvcc():
