@@ -44,9 +44,12 @@ WORKLOADS = {
                  mesh=lambda: synth.icosphere(3), k=16, seed_stream=1, steps=300, dtype="f32"),
 }
 
-# DRAM bytes of one step-kernel launch from an ncu capture of the grid512
-# workload, valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"kernel_sha": "6932ba2487f95031", "bytes_per_launch": 17856939}
+# Counters of one step-kernel launch from an ncu capture of the grid512
+# workload (FP32 field, steady state): DRAM bytes and warp instructions.
+# Valid only for that workload and the kernel source they were taken on.
+NCU_COUNTERS = {"workload": "grid512", "dtype": "f32", "kernel_sha": "6932ba2487f95031",
+                "bytes_per_launch": 17856939, "warp_instructions_per_launch": 13613993}
+SM_COUNT, SUBPARTITIONS = 152, 4          # GB300: 152 SMs, 4 schedulers each issuing one warp instruction a cycle
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -233,6 +236,7 @@ def run_ours(args, wl):
         wall = time.perf_counter() - wall0
         st = mesh.stats()
 
+    clk_summary = clk.summary()
     t_job = sum(job_ms) / 1e3
     t_all, units_all = aggregate(dist, t_job, units, "cuda")
     value = units_all / t_all
@@ -245,11 +249,23 @@ def run_ours(args, wl):
     t_step = sum(step_ms) / 1e3
     achieved = bytes_total / t_step / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel_sha"] == kernel_sha() else None
+    counters = (NCU_COUNTERS if NCU_COUNTERS["kernel_sha"] == kernel_sha() and args.workload == NCU_COUNTERS["workload"]
+                and wl["dtype"] == NCU_COUNTERS["dtype"] else None)
+    traffic = counters["bytes_per_launch"] if counters else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_total / launches,
                 "us_per_launch": 1e6 * t_step / launches}
+    if counters:
+        # the bound that binds: instruction issue (ncu's warp-instruction count
+        # per launch over the event-timed launch, against one warp instruction
+        # per scheduler and cycle at the SM clock sampled during the run)
+        mhz = clk_summary.get("sm_mhz") or clk_summary.get("sm_max_mhz") or 2070.0
+        peak_issue = SM_COUNT * SUBPARTITIONS * mhz * 1e6
+        issued = counters["warp_instructions_per_launch"] / (t_step / launches)
+        roofline["issue"] = {"achieved": issued / 1e12, "peak": peak_issue / 1e12, "unit": "T warp-instr/s",
+                             "frac": issued / peak_issue,
+                             "warp_instructions_per_launch": counters["warp_instructions_per_launch"]}
 
     # end to end through the C ABI from host buffers: create (host cotan build +
     # upload), seed, steps, labels back to the host, destroy
@@ -284,7 +300,7 @@ def run_ours(args, wl):
         "e2e": {"value": e2e_units / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "jobs": n_e2e},
         "gpu_launches": args.steps * (T + 4) + retries,   # seed (fill, scatter, head records), steps, labels
-        "clocks": clk.summary(),
+        "clocks": clk_summary,
         "wall_s": wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
