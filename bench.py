@@ -411,7 +411,7 @@ def run_batch(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind},
         "e2e": {"value": e2e_units / t_e2e, "unit": UNIT,
-                "h2d_bytes_per_step": int(sum(4 * (m.n_v + 1) + 8 * s["operator_nnz"] for s, m in zip(sts, geo))),
+                "h2d_bytes_per_step": int(sum(24 * m.n_v + 12 * m.n_f + 4 * len(sd) for m, sd in zip(geo, seeds))),
                 "d2h_bytes_per_step": int(4 * n_v_total), "jobs": len(specs)},
         "gpu_launches": args.steps * T * 2,
         "clocks": clk.summary(),
