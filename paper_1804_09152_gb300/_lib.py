@@ -13,8 +13,11 @@ import os
 
 import numpy as np
 
-from .native import LIB
+from .native import LIB as _DEFAULT_LIB
 
+# LF_LIBRARY selects another build of the same sources (the bounds-checked
+# test build); there is no other implementation to fall back to.
+LIB = os.environ.get("LF_LIBRARY") or _DEFAULT_LIB
 if not os.path.exists(LIB):
     raise ImportError(f"CUDA library {LIB} is missing: run paper_1804_09152_gb300.build() first")
 

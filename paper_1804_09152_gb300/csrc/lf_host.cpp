@@ -361,6 +361,12 @@ lf_status set_tile_cap(lf_mesh m, int64_t new_cap, bool keep) {
   return upload_job(m);
 }
 
+// Why a step failed for good (the device error bits other than capacity).
+const char* failed_step_message(uint32_t err) {
+  if (err & lf::ERR_BOUNDS) return "an index left its array (reported by a checked build)";
+  return "a vertex summed to zero before normalisation";
+}
+
 // A graph of independent chains, each of kGraphSteps step launches of one
 // storage type (chain c launches chains[c].second with step = 0, 1, ...).
 // Within a chain each launch is joined to the previous one by a programmatic
@@ -534,6 +540,7 @@ lf_status finish_setup(lf_mesh m, const lf_params& prm) {
   j.buf[0] = m->buf[0];
   j.buf[1] = m->buf[1];
   j.st = m->d_st;
+  j.L_nnz = static_cast<int32_t>(m->L_nnz);
   j.c = lf::Coefs{static_cast<float>(prm.dt),   static_cast<float>(prm.mu),   static_cast<float>(prm.w_cc),
                   static_cast<float>(prm.w_cb), static_cast<float>(prm.a_cc), static_cast<float>(prm.a_cb),
                   static_cast<float>(prm.e_cc), static_cast<float>(prm.e_cb), static_cast<float>(prm.e_bc)};
@@ -890,9 +897,9 @@ lf_status lf_step(lf_mesh m, int32_t n_iters) {
 
     // a step failed: the field is intact in buf[epoch & 1]; fix and re-run
     const uint32_t err = m->h_st.err;
-    if (err & lf::ERR_ZERO_SUM) {
+    if (err & (lf::ERR_ZERO_SUM | lf::ERR_BOUNDS)) {
       reset_after_failure(m);
-      return fail(m, LF_ERR_STATE, "a vertex summed to zero before normalisation");
+      return fail(m, LF_ERR_STATE, failed_step_message(err));
     }
     if (err & lf::ERR_CAPACITY) {
       const int64_t need = static_cast<int64_t>(m->h_st.need_tile);
@@ -1009,10 +1016,11 @@ lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters) {
       if (s != LF_OK) { drop_graph(); return s; }
       m->steps = static_cast<int64_t>(m->h_st.epoch);
       if (m->h_st.err == 0u) continue;
-      if (m->h_st.err & lf::ERR_ZERO_SUM) {
+      if (m->h_st.err & (lf::ERR_ZERO_SUM | lf::ERR_BOUNDS)) {
+        const uint32_t err = m->h_st.err;
         reset_after_failure(m);
         target[static_cast<size_t>(a)] = m->steps;          // leave it out of the rest of the batch
-        result = fail(m, LF_ERR_STATE, "a vertex summed to zero before normalisation");
+        result = fail(m, LF_ERR_STATE, failed_step_message(err));
         continue;
       }
       const int64_t need = static_cast<int64_t>(m->h_st.need_tile);

@@ -16,6 +16,7 @@ namespace lf {
 enum : uint32_t {
   ERR_CAPACITY = 1u,   // a tile's output would exceed its segment of the field buffer
   ERR_ZERO_SUM = 8u,   // a vertex summed to zero before normalisation
+  ERR_BOUNDS = 16u,    // an index outside its array (builds with LF_CHECKED only)
 };
 
 // Per-mesh device status.  The step kernel reads err and epoch at entry; the
@@ -75,7 +76,7 @@ struct JobDesc {
   const float* cA;
   const float* cE;
   Coefs c;
-  int32_t pad;
+  int32_t L_nnz;             // entries of L_colval (bounds of the checked build)
 };
 
 // Parameters of one step launch: up to kMaxJobs jobs whose tiles are laid

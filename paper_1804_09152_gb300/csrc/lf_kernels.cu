@@ -211,6 +211,17 @@ __device__ __forceinline__ void add_to_sums(VertexSums& s, bool is_base, float f
 }
 
 
+// Checked builds (-DLF_CHECKED) test every index the step kernel reads or
+// writes through against its array; one outside raises ERR_BOUNDS in the
+// job's status word and the access goes to element 0 instead, so the kernel
+// never leaves its buffers and the host fails the step.  Other builds compile
+// the checks away.
+#ifdef LF_CHECKED
+#define LF_CK(obj, x, hi) (obj).ck((x), (hi))
+#else
+#define LF_CK(obj, x, hi) (x)
+#endif
+
 // The closed neighbourhood of one vertex, read straight from global memory.
 // Used by the slow path, which enumerates the layer union in increasing id
 // order: next_layer() scans the sorted rows for the smallest id above `cur`,
@@ -225,17 +236,28 @@ struct Neighbourhood {
   const int2* __restrict__ Lcv;
   int p0, p1, q0, q1;
   float dsum;
+#ifdef LF_CHECKED
+  DevStatus* st;
+  int n_v, L_nnz, entries;
+  __device__ int ck(int x, int hi) const {
+    if (static_cast<unsigned>(x) >= static_cast<unsigned>(hi)) {
+      atomicOr(&st->err, ERR_BOUNDS);
+      return 0;
+    }
+    return x;
+  }
+#endif
 
   __device__ int next_layer(int cur) const {
     int nx = 0x7fffffff;
     for (int p = p0; p < p1; ++p) {
-      const int l = __ldg(Fid + p);
+      const int l = __ldg(Fid + LF_CK(*this, p, entries));
       if (l > cur) { nx = min(nx, l); break; }
     }
     for (int q = q0; q < q1; ++q) {
-      const int2 rj = __ldg(rows + __ldg(&Lcv[q].x));
+      const int2 rj = __ldg(rows + LF_CK(*this, __ldg(&Lcv[LF_CK(*this, q, L_nnz)].x), n_v));
       for (int p = rj.x; p < rj.x + rj.y; ++p) {
-        const int l = __ldg(Fid + p);
+        const int l = __ldg(Fid + LF_CK(*this, p, entries));
         if (l > cur) { nx = min(nx, l); break; }
       }
     }
@@ -246,17 +268,17 @@ struct Neighbourhood {
     F = 0.0f;
     G = 0.0f;
     for (int p = p0; p < p1; ++p) {
-      const int l = __ldg(Fid + p);
-      if (l == lay) { F = V::load(Fval + p); break; }
+      const int l = __ldg(Fid + LF_CK(*this, p, entries));
+      if (l == lay) { F = V::load(Fval + LF_CK(*this, p, entries)); break; }
       if (l > lay) break;
     }
     for (int q = q0; q < q1; ++q) {
-      const int2 cv = __ldg(Lcv + q);
+      const int2 cv = __ldg(Lcv + LF_CK(*this, q, L_nnz));
       const float lij = __int_as_float(cv.y);
-      const int2 rj = __ldg(rows + cv.x);
+      const int2 rj = __ldg(rows + LF_CK(*this, cv.x, n_v));
       for (int p = rj.x; p < rj.x + rj.y; ++p) {
-        const int l = __ldg(Fid + p);
-        if (l == lay) { G = __fadd_rn(G, __fmul_rn(lij, V::load(Fval + p))); break; }
+        const int l = __ldg(Fid + LF_CK(*this, p, entries));
+        if (l == lay) { G = __fadd_rn(G, __fmul_rn(lij, V::load(Fval + LF_CK(*this, p, entries)))); break; }
         if (l > lay) break;
       }
     }
@@ -419,6 +441,12 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
   nb.Lcv = J.L_colval;
   nb.dsum = 0.0f;
   nb.p0 = nb.p1 = nb.q0 = nb.q1 = 0;
+#ifdef LF_CHECKED
+  nb.st = J.st;
+  nb.n_v = J.n_v;
+  nb.L_nnz = J.L_nnz;
+  nb.entries = J.num_tiles * J.tile_cap;
+#endif
 
   // the first loads do not depend on the error word: issue them before the
   // barrier that publishes it
@@ -486,8 +514,8 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
         if (s < own) {
-          mp.id[s] = __ldg(nb.Fid + nb.p0 + s);
-          mp.f[s] = V::load(nb.Fval + nb.p0 + s);
+          mp.id[s] = __ldg(nb.Fid + LF_CK(nb, nb.p0 + s, nb.entries));
+          mp.f[s] = V::load(nb.Fval + LF_CK(nb, nb.p0 + s, nb.entries));
         }
       }
     }
@@ -520,7 +548,7 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
         jj[k] = -1;
         lij[k] = 0.0f;
         if (qb + k < nb.q1) {
-          const int2 cv = __ldg(nb.Lcv + qb + k);
+          const int2 cv = __ldg(nb.Lcv + LF_CK(nb, qb + k, nb.L_nnz));
           jj[k] = cv.x;
           lij[k] = __int_as_float(cv.y);
         }
@@ -530,7 +558,7 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
       for (int k = 0; k < kChunk; ++k) {
         hj[k] = make_int4(0, 0, 0, 0);
         if (jj[k] >= 0) {
-          hj[k] = __ldg(in.head + jj[k]);
+          hj[k] = __ldg(in.head + LF_CK(nb, jj[k], nb.n_v));
           nb.dsum += lij[k];
         }
         rn[k] = hj[k].x;
@@ -599,13 +627,16 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
 #pragma unroll
         for (int k = 0; k < kChunk; ++k) {
           if (rn[k] <= 0 || mode != kFast) continue;
-          const int start = rn[k] > 2 ? __ldg(nb.rows + jj[k]).x : 0;
+          const int start = rn[k] > 2 ? __ldg(nb.rows + LF_CK(nb, jj[k], nb.n_v)).x : 0;
           for (int p = 0; p < rn[k] && mode == kFast; ++p) {
             int l;
             float x;
             if (p == 0) { l = e0[k]; x = x0[k]; }
             else if (p == 1) { l = e1[k]; x = x1[k]; }
-            else { l = __ldg(nb.Fid + start + p); x = __fmul_rn(lij[k], V::load(nb.Fval + start + p)); }
+            else {
+              l = __ldg(nb.Fid + LF_CK(nb, start + p, nb.entries));
+              x = __fmul_rn(lij[k], V::load(nb.Fval + LF_CK(nb, start + p, nb.entries)));
+            }
             if (l == base) gB = __fadd_rn(gB, x);
             else if (!mp.add(l, x)) mode = kMedium;
           }
@@ -637,13 +668,15 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
       med.g = s_med_g[slot];
       med.f = s_med_f[slot];
       bool ok = true;
-      for (int p = nb.p0; p < nb.p1; ++p) ok = ok && med.add(__ldg(nb.Fid + p), 0.0f, V::load(nb.Fval + p));
+      for (int p = nb.p0; p < nb.p1; ++p)
+        ok = ok && med.add(__ldg(nb.Fid + LF_CK(nb, p, nb.entries)), 0.0f, V::load(nb.Fval + LF_CK(nb, p, nb.entries)));
       for (int q = nb.q0; q < nb.q1 && ok; ++q) {
-        const int2 cv = __ldg(nb.Lcv + q);
+        const int2 cv = __ldg(nb.Lcv + LF_CK(nb, q, nb.L_nnz));
         const float lij = __int_as_float(cv.y);
-        const int2 rj = __ldg(nb.rows + cv.x);
+        const int2 rj = __ldg(nb.rows + LF_CK(nb, cv.x, nb.n_v));
         for (int p = rj.x; p < rj.x + rj.y && ok; ++p)
-          ok = med.add(__ldg(nb.Fid + p), __fmul_rn(lij, V::load(nb.Fval + p)), 0.0f);
+          ok = med.add(__ldg(nb.Fid + LF_CK(nb, p, nb.entries)),
+                       __fmul_rn(lij, V::load(nb.Fval + LF_CK(nb, p, nb.entries))), 0.0f);
       }
       if (ok) {
         mode = kMedium;
@@ -866,8 +899,13 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
     // head record: the count and the first two entries written
     int4 ho = make_int4(kept, 0, 0, 0);
     auto put = [&](int o, int l, T vt) {
-      out.ids[o] = static_cast<uint16_t>(l);
-      ov[o] = vt;
+#ifdef LF_CHECKED
+      const int w = tile * cap + nb.ck(o - tile * cap, cap);   // inside the tile's segment
+#else
+      const int w = o;
+#endif
+      out.ids[w] = static_cast<uint16_t>(l);
+      ov[w] = vt;
       if (o == off) { ho.y = l; ho.z = V::bits(vt); }
       else if (o == off + 1) { ho.y |= l << 16; ho.w = V::bits(vt); }
     };

@@ -12,6 +12,7 @@
 
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -119,6 +120,7 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers, cons
   job.buf[1] = lf::FieldBuf{reinterpret_cast<int2*>(d_rows_out), reinterpret_cast<int4*>(d_head_out), d_ids_out,
                             d_vals_out};
   job.st = &d_layout->st;
+  job.L_nnz = INT32_MAX;                          // not known here: no operator bound
   job.c = lf::Coefs{static_cast<float>(p.dt),   static_cast<float>(p.mu),   static_cast<float>(p.w_cc),
                     static_cast<float>(p.w_cb), static_cast<float>(p.a_cc), static_cast<float>(p.a_cb),
                     static_cast<float>(p.e_cc), static_cast<float>(p.e_cb), static_cast<float>(p.e_bc)};
@@ -139,6 +141,8 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers, cons
   if (need_tile_cap) *need_tile_cap = static_cast<int64_t>(st.need_tile);
   if (st.err & lf::ERR_CAPACITY)
     return noalloc_fail(LF_ERR_CAPACITY, "a tile's output exceeds tile_cap; *need_tile_cap entries are needed");
+  if (st.err & lf::ERR_BOUNDS)
+    return noalloc_fail(LF_ERR_STATE, "an index left its array (reported by a checked build)");
   if (st.err != 0u) return noalloc_fail(LF_ERR_STATE, "a vertex summed to zero before normalisation");
   if (nnz_out) *nnz_out = static_cast<int64_t>(st.nnz);
   return LF_OK;

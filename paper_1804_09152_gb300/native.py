@@ -14,6 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblf.so")
+# Test build with every step-kernel index checked against its array (-DLF_CHECKED).
+LIB_CHECKED = os.path.join(BUILD, "liblf_checked.so")
 SOURCES = ["lf_kernels.cu", "lf_lloyd.cu", "lf_dual.cu", "lf_cotan.cu", "lf_host.cpp", "lf_noalloc.cu",
            "lf_server.cpp"]
 HEADERS = [os.path.join(CSRC, "lf_internal.h"), os.path.join(ROOT, "include", "lf.h")]
@@ -35,16 +37,20 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False):
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, checked=False):
+    """Builds liblf.so, or with checked=True the bounds-checked test variant."""
+    lib = LIB_CHECKED if checked else LIB
+    objdir = os.path.join(BUILD, "checked") if checked else BUILD
+    extra = ["-DLF_CHECKED"] if checked else []
+    os.makedirs(objdir, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    if not force and not _stale(LIB, srcs + HEADERS + [__file__]):
-        return LIB
+    if not force and not _stale(lib, srcs + HEADERS + [__file__]):
+        return lib
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
@@ -52,10 +58,10 @@ def build(force=False, verbose=False):
 
     with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -123,3 +123,13 @@ def test_server_and_batch_reject_invalid_input_without_gpu(lib):
     arr = (ctypes.c_void_p * 1)(None)
     assert lib._lib.lf_step_batch(arr, 0, cnt) == lib.LF_ERR_INVALID
     assert lib._lib.lf_step_batch(arr, 1, cnt) == lib.LF_ERR_INVALID      # null mesh
+
+
+def test_checked_build_compiles_and_exports_the_same_symbols():
+    # the bounds-checked variant (-DLF_CHECKED) that the GPU tests compare
+    # with the plain build: same sources, same entry points
+    from paper_1804_09152_gb300 import native
+    path = native.build(checked=True)
+    so = ctypes.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(so, n), n
