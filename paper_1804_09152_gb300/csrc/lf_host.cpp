@@ -713,6 +713,7 @@ void lf_default_params(lf_params* p) {
 
 lf_status lf_create_mesh(const lf_device* dev, const double* V, int64_t n_v, const int32_t* F, int64_t n_f,
                          const lf_params* params, lf_mesh* out) {
+  lf::TraceRange trace("lf_create_mesh");
   if (!out) return fail(nullptr, LF_ERR_INVALID, "null argument");
   lf_params prm;
   lf_default_params(&prm);
@@ -865,6 +866,7 @@ lf_status lf_set_coefficients(lf_mesh m, int32_t n_layers, const float* W, const
 }
 
 lf_status lf_step(lf_mesh m, int32_t n_iters) {
+  lf::TraceRange trace("lf_step");
   lf_status s = check_usable(m);
   if (s != LF_OK) return s;
   if (n_iters < 0) return fail(m, LF_ERR_INVALID, "n_iters must be >= 0");
@@ -918,6 +920,7 @@ lf_status lf_step(lf_mesh m, int32_t n_iters) {
 }
 
 lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters) {
+  lf::TraceRange trace("lf_step_batch");
   if (!meshes || n < 1 || n > lf::kMaxJobs)
     return fail(nullptr, LF_ERR_INVALID, "need 1 <= n <= 64 meshes");
   if (!n_iters) return fail(nullptr, LF_ERR_INVALID, "n_iters is null");
@@ -1366,6 +1369,7 @@ lf_status dual_scratch(lf_mesh m, int64_t k, uint32_t cap) {
 extern "C" {
 
 lf_status lf_extract_dual(lf_mesh m, int32_t* tris, int64_t cap, int64_t* n_tris) {
+  lf::TraceRange trace("lf_extract_dual");
   lf_status s = check_usable(m);
   if (s != LF_OK) return s;
   if (!n_tris) return fail(m, LF_ERR_INVALID, "n_tris must not be NULL");
@@ -1426,6 +1430,7 @@ lf_status lf_extract_dual(lf_mesh m, int32_t* tris, int64_t cap, int64_t* n_tris
 }
 
 lf_status lf_lloyd(lf_mesh m, int32_t rounds, int32_t steps_per_round, int32_t* seeds_out) {
+  lf::TraceRange trace("lf_lloyd");
   lf_status s = check_usable(m);
   if (s != LF_OK) return s;
   if (rounds < 0 || steps_per_round < 0) return fail(m, LF_ERR_INVALID, "rounds and steps_per_round must be >= 0");

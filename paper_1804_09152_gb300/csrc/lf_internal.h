@@ -8,9 +8,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lf.h"
 
 namespace lf {
+
+// NVTX range for the lifetime of a scope (header-only NVTX 3: costs nothing
+// unless a profiler is attached), so that a tool can attribute kernels to
+// the library call that launched them.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Error bits raised on the device (DevStatus::err).
 enum : uint32_t {

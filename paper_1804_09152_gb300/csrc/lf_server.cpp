@@ -147,6 +147,7 @@ void scheduler(lf_server_s* s) {
     }
     // create and seed the admitted jobs (outside the lock: the upload is long)
     for (const JobPtr& j : admit) {
+      lf::TraceRange trace("lf_server admit");
       lf_mesh m = nullptr;
       lf_status r = lf::create_from_offdiag(&s->dev, j->n_v, j->rp, j->col, j->val, j->prm, &m);
       if (r == LF_OK && !j->V.empty())
