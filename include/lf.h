@@ -63,8 +63,9 @@ typedef enum { LF_F32 = 0, LF_BF16 = 1, LF_F16 = 2 } lf_dtype;
  *   e_bc = -0.5 (Eq. 12 is antisymmetric in the pair), iso = 0.25 (Sec. 5.1),
  *   field_dtype = LF_F32, initial_capacity = 0.
  * initial_capacity: entries each field buffer holds before the first growth;
- *   0 picks max(2 n_v, 4096).  Growth is automatic (lf_step), so this only
- *   trades memory against re-runs of a step.
+ *   0 picks three entries per vertex (at least 256 per tile of 256 vertices).
+ *   Growth is automatic (lf_step), so this only trades memory against re-runs
+ *   of a step.
  */
 typedef struct {
   double dt;
@@ -166,9 +167,9 @@ lf_status lf_seed(lf_mesh m, const int32_t* seed_vertices, int32_t k);
 lf_status lf_seed_regions(lf_mesh m, const int32_t* seeds, int32_t k, int32_t rings);
 
 /*
- * General coefficient matrices of Algorithm 1 (Sec. 3.3 states the update
- * for any w_jl, a_jl, e_jk; Sec. 3.4 picks the class values that lf_params
- * holds).  W, A and E are host pointers, each NULL or an n_layers x n_layers
+ * General coefficient matrices of Algorithm 1 (Sec. 3.2: the update is
+ * written for any w_jl, a_jl, e_jk; Sec. 3.1 gives the uniform values that
+ * lf_params holds as two classes).  W, A and E are host pointers, each NULL or an n_layers x n_layers
  * row-major FP32 matrix indexed by layer id (cells 0..k-1, base layer k):
  * W[j * n_layers + l] = w_jl, A[...] = a_jl, E[j * n_layers + k] = e_jk.  A
  * NULL matrix keeps the class rule for that coefficient; all three NULL
