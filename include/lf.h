@@ -376,13 +376,15 @@ lf_status lf_extract_dual(lf_mesh m, int32_t* tris, int64_t cap, int64_t* n_tris
  * yet.  The scheduler admits queued jobs in arrival order while fewer than
  * max_active jobs run and the estimated device bytes of the admitted jobs
  * stay within hbm_budget_bytes (a job larger than the whole budget fails with
- * LF_ERR_OOM), creates and seeds each one (lf_create_mesh, lf_seed), and
- * advances all running jobs together with lf_step_batch in chunks of
- * chunk_steps.  A job asking for Lloyd-like rounds (Sec. 5) gets, each time it
- * has taken its n_iters steps, a seed update and a fresh field, and another
- * n_iters steps in the batches; a job asking for the dual mesh (Sec. 5.2)
- * gets it at the end.  A finished job gets its sharp labels (Sec. 6) copied
- * to the host and its device memory freed; admission then runs again.  A job that fails (e.g. a vertex summing to zero) is retired
+ * LF_ERR_OOM), puts each one on the device (its operator, and its geometry
+ * when it asked for Lloyd-like rounds or the dual mesh) and seeds it (as
+ * lf_seed), and advances all running jobs together with lf_step_batch in
+ * chunks of chunk_steps.  A job asking for Lloyd-like rounds (Sec. 5) gets,
+ * each time it has taken its n_iters steps, a seed update and a fresh field,
+ * and another n_iters steps in the batches; a job asking for the dual mesh
+ * (Sec. 5.2) gets it at the end.  A finished job gets its sharp labels
+ * (Sec. 6) copied to the host and its device memory freed; admission then
+ * runs again.  A job that fails (e.g. a vertex summing to zero) is retired
  * with its status; the others continue.  The paper runs one mesh at a time;
  * this runtime has no counterpart there.
  * ------------------------------------------------------------------------ */
