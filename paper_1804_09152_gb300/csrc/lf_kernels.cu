@@ -604,22 +604,27 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
             hit[k] = hit[k] || m;
           }
         }
-        // cells new to the map, in row order (a layer is new in all of its
-        // entries of the batch or in none)
-        unsigned miss = 0u;
+        // cells new to the map, in row order: a missed entry opens the next
+        // slot (no existing slot can match it: the matrix above compared them
+        // all); when both entries of the batch miss with the same layer, one
+        // slot opens with their sum taken in row order
+        static_assert(kChunk == 2, "the miss handling below is written for batches of two");
+        const bool m0 = !hit[0], m1 = !hit[1];
+        if (m0 || m1) {
+          const bool same = m0 && m1 && e0[0] == e0[1];
+          const int la = m0 ? e0[0] : e0[1];
+          const float xa = m0 ? (same ? __fadd_rn(x0[0], x0[1]) : x0[0]) : x0[1];
+          const bool second = m0 && m1 && !same;
+          if (mp.cnt + (second ? 1 : 0) >= kSlots - 1) {
+            mode = kMedium;                    // one slot stays for the base layer
+          } else {
 #pragma unroll
-        for (int k = 0; k < kChunk; ++k) miss |= hit[k] ? 0u : (1u << k);
-        while (miss != 0u && mode == kFast) {
-          const int k = __ffs(miss) - 1;
-          miss &= miss - 1u;
-          int le = -2;
-          float xe = 0.0f;
-#pragma unroll
-          for (int q = 0; q < kChunk; ++q) {
-            le = (q == k) ? e0[q] : le;
-            xe = (q == k) ? x0[q] : xe;
+            for (int s2 = 0; s2 < kSlots - 1; ++s2) {
+              if (s2 == mp.cnt) { mp.id[s2] = la; mp.g[s2] = xa; }
+              if (second && s2 == mp.cnt + 1) { mp.id[s2] = e0[1]; mp.g[s2] = x0[1]; }
+            }
+            mp.cnt += second ? 2 : 1;
           }
-          if (!mp.add(le, xe)) mode = kMedium;
         }
       } else {
         // rows with two cells or more than two entries (transients, band
