@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lf_internal.h"
 
 namespace lf {
@@ -344,6 +346,18 @@ struct SlotMap {
     g[a] = sw ? gb : ga;  g[b] = sw ? ga : gb;
     f[a] = sw ? fb : fa;  f[b] = sw ? fa : fb;
   }
+  // The first M slots in ascending id order (empty slots, -1, last): the
+  // warp's lanes use at most M slots, so the rest are empty everywhere.
+  template <int M>
+  __device__ __forceinline__ void sort_first() {
+    if constexpr (M == 2) {
+      cswap(0, 1);
+    } else if constexpr (M == 3) {
+      cswap(0, 1); cswap(1, 2); cswap(0, 1);
+    } else if constexpr (M >= 4) {
+      sort();
+    }
+  }
   // Sorting network on the cell slots (ids are distinct; empty slots hold -1,
   // which sorts last).  The base layer, the largest id, is the last live
   // slot, so ordering the first kSlots - 1 slots orders them all: the optimal
@@ -359,6 +373,21 @@ struct SlotMap {
     }
   }
 };
+
+// Runs fn with the number of register slots a warp's lanes use at most as a
+// compile-time constant, so that the per-slot loops after the gather unroll
+// over the live slots only (n is warp-uniform).
+static_assert(kSlots == 5, "with_slots spells out the slot counts 1 to 5");
+template <class Fn>
+__device__ __forceinline__ void with_slots(int n, Fn&& fn) {
+  switch (n) {
+    case 1: fn(std::integral_constant<int, 1>{}); break;
+    case 2: fn(std::integral_constant<int, 2>{}); break;
+    case 3: fn(std::integral_constant<int, 3>{}); break;
+    case 4: fn(std::integral_constant<int, 4>{}); break;
+    default: fn(std::integral_constant<int, 5>{}); break;
+  }
+}
 
 // Medium path: a map of kMed slots in shared memory, one of kPool per CTA,
 // taken by the (rare) threads whose union outgrows the register map.
@@ -708,33 +737,38 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
   if (i < n_v) {
     if (mode == kFast) {
       // ---- fast path: diagonal, skeleton, update over the register map ------
+      // over the slots that the lanes here use at most (every lane's own
+      // count is within it, whichever lanes run this together)
+      // (the general form keeps all slots: its matrix sums are the cost there)
+      with_slots(GEN ? kSlots : __reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
+      constexpr int N = decltype(slots)::value;
       // diagonal: the own entries (the own cells, then the base layer)
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s)
+      for (int s = 0; s < N; ++s)
         if (s < own_cells || (s == mp.cnt - 1 && own_cells < own)) mp.g[s] = fmaf(-nb.dsum, mp.f[s], mp.g[s]);
       // slots in ascending layer order (empty slots, id -1, last): the sums
       // below then run in the same order as on the other paths, and the row
       // is written in slot order
-      mp.sort();
-      float sq[kSlots];
+      mp.template sort_first<(N < kSlots - 1 ? N : kSlots - 1)>();
+      float sq[N];
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) sq[s] = root(mp.f[s]);
-      bool ins[kSlots];
+      for (int s = 0; s < N; ++s) sq[s] = root(mp.f[s]);
+      bool ins[N];
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
+      for (int s = 0; s < N; ++s) {
         ins[s] = s < mp.cnt && in_skeleton(mp.f[s], mp.g[s]);
         if (ins[s]) add_to_sums(S, mp.id[s] == base, mp.f[s], mp.g[s], sq[s]);
       }
       if (general) {
         const float fn = static_cast<float>(S.nC + S.hasb);
-        float Aj[kSlots], Wj[kSlots], Ej[kSlots];
+        float Aj[N], Wj[N], Ej[N];
         float sumA = 0.0f, sumW = 0.0f;
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) {
+        for (int s = 0; s < N; ++s) {
           Aj[s] = Wj[s] = Ej[s] = 0.0f;
           if (ins[s]) {
 #pragma unroll
-            for (int l = 0; l < kSlots; ++l) {
+            for (int l = 0; l < N; ++l) {
               if (ins[l]) {
                 Aj[s] = __fmaf_rn(gc.a(mp.id[s], mp.id[l]), mp.g[l], Aj[s]);
                 Wj[s] = __fmaf_rn(gc.w(mp.id[s], mp.id[l]), mp.f[l], Wj[s]);
@@ -746,7 +780,7 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
           }
         }
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) {
+        for (int s = 0; s < N; ++s) {
           if (ins[s]) {
             vnew[s] = gc.value(mp.f[s], sq[s], Aj[s], Wj[s], Ej[s], sumA, sumW, fn);
             tot += vnew[s];
@@ -755,7 +789,7 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
       } else {
         const Update U(S, c);
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) {
+        for (int s = 0; s < N; ++s) {
           if (ins[s]) {
             vnew[s] = U.value(mp.id[s] == base, mp.f[s], mp.g[s], sq[s], S, c);
             tot += vnew[s];
@@ -765,12 +799,13 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
       if (!(tot > 0.0f)) zero_sum = true;
       const float rtot = 1.0f / tot;           // normalisation: one division per vertex
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
+      for (int s = 0; s < N; ++s) {
         if (ins[s]) {
           const float vs = V::widen(V::round(__fmul_rn(vnew[s], rtot)));
           if (vs != 0.0f) { keep[s] = true; vnew[s] = vs; ++kept; }
         }
       }
+      });
     } else if (mode == kMedium) {
       // ---- medium path: the same update over the shared-memory map ----------
       for (int s = 0; s < med.cnt; ++s)
@@ -915,13 +950,18 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
       else if (o == off + 1) { ho.y |= l << 16; ho.w = V::bits(vt); }
     };
     if (mode == kFast) {
-      int o = off;
+      int top = 1;                             // slots up to the last kept one
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
-        if (!keep[s]) continue;
-        put(o, mp.id[s], V::round(vnew[s]));
-        ++o;
-      }
+      for (int s = 0; s < kSlots; ++s) top = keep[s] ? s + 1 : top;
+      with_slots(GEN ? kSlots : __reduce_max_sync(__activemask(), top), [&](auto slots) {
+        int o = off;
+#pragma unroll
+        for (int s = 0; s < decltype(slots)::value; ++s) {
+          if (!keep[s]) continue;
+          put(o, mp.id[s], V::round(vnew[s]));
+          ++o;
+        }
+      });
     } else if (mode == kMedium) {
       int o = off;
       for (int s = 0; s < med.cnt; ++s) {
