@@ -624,15 +624,23 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
         bool hit[kChunk];
 #pragma unroll
         for (int k = 0; k < kChunk; ++k) hit[k] = e0[k] < 0;
+        // over the cell slots that the lanes here have opened at most (the
+        // slots beyond are empty in every lane)
+        auto matrix = [&](auto cells) {
 #pragma unroll
-        for (int s2 = 0; s2 < kSlots - 1; ++s2) {   // cells: the base slot comes last
+          for (int s2 = 0; s2 < decltype(cells)::value; ++s2) {
 #pragma unroll
-          for (int k = 0; k < kChunk; ++k) {
-            const bool m = e0[k] == mp.id[s2];
-            mp.g[s2] = m ? __fadd_rn(mp.g[s2], x0[k]) : mp.g[s2];
-            hit[k] = hit[k] || m;
+            for (int k = 0; k < kChunk; ++k) {
+              const bool m = e0[k] == mp.id[s2];
+              mp.g[s2] = m ? __fadd_rn(mp.g[s2], x0[k]) : mp.g[s2];
+              hit[k] = hit[k] || m;
+            }
           }
-        }
+        };
+        const int open_cells = __reduce_max_sync(__activemask(), mp.cnt);
+        if (open_cells <= 1) matrix(std::integral_constant<int, 1>{});
+        else if (open_cells == 2) matrix(std::integral_constant<int, 2>{});
+        else matrix(std::integral_constant<int, kSlots - 1>{});
         // cells new to the map, in row order: a missed entry opens the next
         // slot (no existing slot can match it: the matrix above compared them
         // all); when both entries of the batch miss with the same layer, one
