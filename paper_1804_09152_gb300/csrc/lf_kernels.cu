@@ -911,9 +911,7 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
     if (lane >= o) x += y;
   }
   // the skeleton sizes are reduced per warp alongside, so one barrier serves both
-  unsigned sk = static_cast<unsigned>(nsk);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sk += __shfl_xor_sync(0xffffffffu, sk, o);
+  const unsigned sk = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(nsk));
   if (lane == 31) {
     s_warp_cnt[warp] = x;
     s_red[warp] = sk;
