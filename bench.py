@@ -51,8 +51,8 @@ WORKLOADS = {
 # Counters of one step-kernel launch from an ncu capture of the grid512
 # workload (FP32 field, steady state): DRAM bytes and warp instructions.
 # Valid only for that workload and the kernel source they were taken on.
-NCU_COUNTERS = {"workload": "grid512", "dtype": "f32", "kernel_sha": "ff07d25bf9042f7b",
-                "bytes_per_launch": 17869568, "warp_instructions_per_launch": 11820107}
+NCU_COUNTERS = {"workload": "grid512", "dtype": "f32", "kernel_sha": "84b3ef791e2bacd0",
+                "bytes_per_launch": 17869056, "warp_instructions_per_launch": 11762763}
 SM_COUNT, SUBPARTITIONS = 152, 4          # GB300: 152 SMs, 4 schedulers each issuing one warp instruction a cycle
 L2_FLUSH_BYTES = 512 << 20
 
