@@ -449,6 +449,25 @@ def cell_area_stats(m, labels, k):
             "empty_cells": int((area == 0).sum()), "base_vertices": int((~cov).sum())}
 
 
+def dual_quality(V, tris):
+    """Triangle quality of a dual mesh as the paper's table of extraction
+    metrics reports it: 2 r_in / r_circ (1 for an equilateral triangle; mean
+    and minimum), the mean and minimum of the smallest angle per triangle,
+    and the share of angles below 30 degrees."""
+    P = np.asarray(V)[np.asarray(tris)]
+    a = np.linalg.norm(P[:, 1] - P[:, 2], axis=1)
+    b = np.linalg.norm(P[:, 2] - P[:, 0], axis=1)
+    c = np.linalg.norm(P[:, 0] - P[:, 1], axis=1)
+    area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    q = 2.0 * (2.0 * area / (a + b + c)) / (a * b * c / (4.0 * area))
+    cos = np.stack([(b * b + c * c - a * a) / (2 * b * c), (c * c + a * a - b * b) / (2 * c * a),
+                    (a * a + b * b - c * c) / (2 * a * b)], 1)
+    ang = np.degrees(np.arccos(np.clip(cos, -1.0, 1.0)))
+    return {"triangles": int(len(tris)), "mean_quality": float(q.mean()), "min_quality": float(q.min()),
+            "mean_min_angle": float(ang.min(1).mean()), "min_angle": float(ang.min()),
+            "angles_below_30_pct": float(100.0 * (ang < 30.0).mean())}
+
+
 def run_lloyd(args):
     """C2 with the paper's full pipeline (Sec. 5): 2000 steps, then Lloyd-like
     rounds (seed update + 2000 steps each), then the dual mesh (Sec. 5.2)."""
@@ -499,13 +518,18 @@ def run_lloyd(args):
                 flush.zero_()
                 torch.cuda.synchronize()
                 res.append(pipeline())
-        # cell areas before and after the rounds (untimed run of the same pipeline)
+        # cell areas and dual-mesh quality before, after one and after all
+        # rounds (untimed run of the same pipeline)
         mesh.seed(seeds)
         mesh.step(T)
         areas = [cell_area_stats(m, mesh.labels(), wl["k"])]
-        for _ in range(R):
+        quality = {"0": dual_quality(m.V, mesh.extract_dual())}
+        for r in range(R):
             mesh.lloyd(1, T)
+            if r == 0:
+                quality["1"] = dual_quality(m.V, mesh.extract_dual())
         areas.append(cell_area_stats(m, mesh.labels(), wl["k"]))
+        quality[str(R)] = dual_quality(m.V, mesh.extract_dual())
         mesh.close()
     total_ms = sum(r[0] for r in res)
     units = sum(r[3] for r in res)
@@ -520,6 +544,7 @@ def run_lloyd(args):
         "dual_extraction_ms": statistics.mean(r[2] for r in res),
         "dual_triangles": res[-1][4],
         "cell_areas": {"before_lloyd": areas[0], f"after_{R}_rounds": areas[1]},
+        "dual_quality_by_rounds": quality,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
