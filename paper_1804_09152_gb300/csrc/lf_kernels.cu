@@ -3,13 +3,15 @@
 // One thread owns one vertex i.  It gathers the closed neighbourhood of i
 // from L (CSR, off-diagonal only) and the field F (CSR, layer ids sorted),
 // accumulating G = L F (the paper's L_t = Phi L^T, Algorithm 1) per layer in
-// a four-slot register map; applies the interest-skeleton test, the explicit
-// Euler update of Eq. 11-13 in closed form, the clamp and the normalisation
-// (Sec. 4); and writes the surviving entries of row i into the output CSR.
-// A vertex whose neighbourhood holds more layers than the map takes a slow
-// path that enumerates the layer union in increasing id order by repeated
-// minimum search over the same rows, so any union size is exact without
-// extra storage.
+// a register map of four cell slots and the base layer; applies the
+// interest-skeleton test, the explicit Euler update of Eq. 11-13 in closed
+// form, the clamp and the normalisation (Sec. 4); and writes the surviving
+// entries of row i into the output CSR.  A vertex whose neighbourhood holds
+// more layers than the map re-gathers into a map in shared memory, and past
+// that takes a path that enumerates the layer union in increasing id order
+// by repeated minimum search over the same rows, so any union size is exact
+// without extra storage.  Every tier sums in the same order with explicitly
+// rounded operations: a vertex's bits do not depend on its tier.
 //
 // The field is a tile-segmented CSR: the 256 vertices of a tile (one CTA)
 // write their rows one after another into the tile's own segment, row
