@@ -1,8 +1,9 @@
 """ctypes binding of the C ABI in ``include/lf.h`` (argument marshalling only).
 
 Every function here has the name of the C entry point it calls and does no
-layered-field arithmetic: the work runs in ``_build/liblf.so``.  Importing this
-module raises if the library has not been built; there is no fallback.
+layered-field arithmetic: the work runs in ``_build/liblf.so`` (or the build of
+the same sources that LF_LIBRARY names).  Importing this module raises if the
+library has not been built; there is no fallback.
 
 Device memory and streams may come from PyTorch: ``torch_device()`` returns an
 ``lf_device`` that allocates through the caching allocator of the current

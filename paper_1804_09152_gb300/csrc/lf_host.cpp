@@ -1,5 +1,8 @@
-// Host side of the layered-field library: mesh operator, device buffers,
-// the step driver (CUDA graphs, overflow recovery) and the C ABI of lf.h.
+// Host side of the layered-field library: mesh validation, the host builder
+// of the cotangent operator (used by the serving path; lf_create_mesh builds
+// it on the device, lf_cotan.cu), device buffers, the step driver (CUDA
+// graphs, overflow recovery), the Lloyd-like and dual-mesh drivers and the C
+// ABI of lf.h.
 
 #include <cuda_runtime.h>
 
