@@ -32,6 +32,12 @@ import synth  # noqa: E402
 METRIC = "field nnz-updates/s and HBM GB/s (% of peak) vs plain; p50/p99 job latency"
 UNIT = "nnz-updates/s"
 
+def _reordered(m, method="rcm"):
+    from paper_1804_09152_gb300.ordering import locality_order
+    V, F, _ = locality_order(m.V, m.F, method)
+    return synth.Mesh(V, F)
+
+
 WORKLOADS = {
     "grid512": dict(desc="planar grid 512x512, alternating diagonals, jitter U(-0.2,0.2) (stream 2), "
                          "1024 seeds (stream 3), FP32 field, 2000 time steps",
@@ -44,6 +50,18 @@ WORKLOADS = {
                            "the size of the paper's largest model), value noise as torus1024, 10000 seeds "
                            "(stream 5), FP32 field, 2000 time steps",
                       mesh=lambda: synth.noisy_torus(3300), k=10000, seed_stream=5, steps=2000, dtype="f32"),
+    "grid512_shuffled": dict(desc="the grid512 mesh with its vertices renumbered by a random permutation "
+                                  "(stream 21), 1024 seeds (stream 3), FP32 field, 2000 time steps",
+                             mesh=lambda: synth.shuffled(synth.planar_grid(512, jitter=0.2, seed=2)), k=1024,
+                             seed_stream=3, steps=2000, dtype="f32"),
+    "grid512_reordered": dict(desc="grid512_shuffled renumbered by reverse Cuthill-McKee (ordering.locality_order), "
+                                   "1024 seeds (stream 3), FP32 field, 2000 time steps",
+                              mesh=lambda: _reordered(synth.shuffled(synth.planar_grid(512, jitter=0.2, seed=2))),
+                              k=1024, seed_stream=3, steps=2000, dtype="f32"),
+    "grid512_morton": dict(desc="grid512_shuffled renumbered along a Morton curve of the positions, 1024 seeds "
+                                "(stream 3), FP32 field, 2000 time steps",
+                           mesh=lambda: _reordered(synth.shuffled(synth.planar_grid(512, jitter=0.2, seed=2)), "morton"),
+                           k=1024, seed_stream=3, steps=2000, dtype="f32"),
     "ico3": dict(desc="icosphere level 3 (642 vertices), 16 seeds (stream 1), FP32 field, 300 time steps",
                  mesh=lambda: synth.icosphere(3), k=16, seed_stream=1, steps=300, dtype="f32"),
 }

@@ -185,3 +185,15 @@ def noisy_torus(n, R=1.0, r=0.35, amp=0.02, seed=4, octaves=4):
     V = ctr + nrm * np.reshape(disp, (-1, 1))
     return Mesh(V, _grid_faces(n, n, periodic=True), name=f"torus{n}",
                 meta={"kind": "torus", "n": n, "R": R, "r": r, "amp": amp, "seed": seed})
+
+
+def shuffled(mesh, seed=21):
+    """The same mesh with its vertices renumbered by a seeded random
+    permutation (faces keep their orientation): a numbering without locality,
+    as a scan or an edited mesh may have."""
+    u = uniform01(seed, np.arange(mesh.n_v, dtype=np.uint64))
+    old_of_new = np.argsort(u, kind="stable")
+    new_of_old = np.empty_like(old_of_new)
+    new_of_old[old_of_new] = np.arange(mesh.n_v)
+    return Mesh(np.ascontiguousarray(mesh.V[old_of_new]), new_of_old[mesh.F].astype(np.int32),
+                name=mesh.name, meta={"new_of_old": new_of_old})
