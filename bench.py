@@ -32,6 +32,24 @@ import synth  # noqa: E402
 METRIC = "field nnz-updates/s and HBM GB/s (% of peak) vs plain; p50/p99 job latency"
 UNIT = "nnz-updates/s"
 
+def _general_coefs(n):
+    """Dense coefficient matrices for n layers: the class values of the default
+    parameters (base layer n - 1) plus a seeded perturbation of +-0.025 (stream 31)."""
+    cell = np.arange(n) < n - 1
+    both = np.outer(cell, cell)
+    W = np.where(both, 0.2, 0.0)
+    A = np.full((n, n), 0.04)
+    E = np.zeros((n, n))
+    E[cell, n - 1] = 0.5
+    E[n - 1, cell] = -0.5
+    out = []
+    for t, M in enumerate((W, A, E)):
+        np.fill_diagonal(M, 0.0)
+        u = synth.uniform01(31, np.arange(t * n * n, (t + 1) * n * n, dtype=np.uint64)).reshape(n, n)
+        out.append((M + 0.05 * (u - 0.5)).astype(np.float32))
+    return out
+
+
 def _reordered(m, method="rcm"):
     from paper_1804_09152_gb300.ordering import locality_order
     V, F, _ = locality_order(m.V, m.F, method)
@@ -62,6 +80,11 @@ WORKLOADS = {
                                 "(stream 3), FP32 field, 2000 time steps",
                            mesh=lambda: _reordered(synth.shuffled(synth.planar_grid(512, jitter=0.2, seed=2)), "morton"),
                            k=1024, seed_stream=3, steps=2000, dtype="f32"),
+    "grid512_general": dict(desc="grid512 with dense general coefficient matrices (the class values perturbed "
+                                 "by +-0.025, stream 31; 1025 x 1025 each), 1024 seeds (stream 3), FP32 field, "
+                                 "2000 time steps",
+                            mesh=lambda: synth.planar_grid(512, jitter=0.2, seed=2), k=1024, seed_stream=3,
+                            steps=2000, dtype="f32", coefs=_general_coefs),
     "ico3": dict(desc="icosphere level 3 (642 vertices), 16 seeds (stream 1), FP32 field, 300 time steps",
                  mesh=lambda: synth.icosphere(3), k=16, seed_stream=1, steps=300, dtype="f32"),
 }
@@ -168,10 +191,11 @@ def oracle_sample(wl, n_steps):
     m = wl["mesh"]()
     L = oracle.cotan_laplacian(m.V, m.F)
     F = oracle.seed(m.n_v, synth.sample_seeds(m.n_v, wl["k"], wl["seed_stream"]))
+    mats = [M.astype(np.float64) for M in wl["coefs"](wl["k"] + 1)] if wl.get("coefs") else (None, None, None)
     units, done = 0, 0
     t0 = time.perf_counter()
     while done < n_steps and time.perf_counter() - t0 < ORACLE_SAMPLE_SECONDS:
-        F, sk = oracle.step(L, F)
+        F, sk = oracle.step(L, F, W=mats[0], A=mats[1], E=mats[2])
         units += sk
         done += 1
     dt = time.perf_counter() - t0
@@ -227,6 +251,10 @@ def run_ours(args, wl):
     with torch.cuda.stream(stream):
         dev = lf.torch_device(stream)
         mesh = lf.Mesh(m.V, m.F, device=dev, field_dtype=wl["dtype"])
+        coefs = wl["coefs"](wl["k"] + 1) if wl.get("coefs") else None
+        if coefs is not None:
+            mesh.seed(seeds)
+            mesh.set_coefficients(*coefs)          # kept across the re-seeding of every job
 
         def job():
             mesh.seed(seeds)
@@ -310,6 +338,8 @@ def run_ours(args, wl):
             t0 = time.perf_counter()
             mm = lf.Mesh(m.V, m.F, device=lf.torch_device(stream), field_dtype=wl["dtype"])
             mm.seed(seeds)
+            if coefs is not None:
+                mm.set_coefficients(*coefs)
             mm.step(T)
             lab = mm.labels()
             s = mm.stats()
@@ -318,6 +348,8 @@ def run_ours(args, wl):
             e2e_t += time.perf_counter() - t0
             e2e_units += s["skeleton_total"]
     h2d = 24 * m.n_v + 12 * m.n_f + 4 * wl["k"]          # vertices, faces, seeds (the operator is built on the device)
+    if coefs is not None:
+        h2d += sum(M.nbytes for M in coefs)
     d2h = 4 * m.n_v
 
     line = {
