@@ -205,3 +205,34 @@ def test_coefficient_lifetime_and_errors(lf):
         mesh.seed(seeds)
         mesh.step(120)
         assert all(np.array_equal(x, y) for x, y in zip(plain, mesh.get_field()))
+
+
+def test_reduced_storage_with_matrices_is_bit_exact_in_a_batch(lf):
+    # the general form of the BF16 and FP16 kernels: each mesh in a batch
+    # (with a class-coefficient FP32 mesh beside them) equals its run alone
+    g = synth.planar_grid(61, seed=2)
+    t = synth.noisy_torus(40)
+    mats = perturbed(33, 12)
+    runs = [(g, synth.sample_seeds(g.n_v, 32, 3), "bf16", mats), (t, synth.sample_seeds(t.n_v, 32, 5), "f16", mats),
+            (synth.icosphere(3), synth.sample_seeds(642, 16, 1), "f32", None)]
+    want = []
+    for m, sd, dt, M in runs:
+        with lf.Mesh(m.V, m.F, field_dtype=dt) as mesh:
+            mesh.seed(sd)
+            if M is not None:
+                mesh.set_coefficients(*M)
+            mesh.step(150)
+            want.append(mesh.get_field())
+    meshes = [lf.Mesh(m.V, m.F, field_dtype=dt) for m, _, dt, _ in runs]
+    try:
+        for mesh, (m, sd, dt, M) in zip(meshes, runs):
+            mesh.seed(sd)
+            if M is not None:
+                mesh.set_coefficients(*M)
+        lf.lf_step_batch(meshes, 150)
+        for mesh, w in zip(meshes, want):
+            for x, y in zip(w, mesh.get_field()):
+                assert np.array_equal(x, y)
+    finally:
+        for mesh in meshes:
+            mesh.close()
