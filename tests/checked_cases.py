@@ -19,19 +19,7 @@ for p in (ROOT, os.path.join(ROOT, "tests")):
         sys.path.insert(0, p)
 
 import synth  # noqa: E402
-
-
-def random_field(n_v, n_layers, per_row, rng):
-    rp, ids, vals = [0], [], []
-    for _ in range(n_v):
-        r = int(rng.integers(1, per_row + 1))
-        ls = np.sort(rng.choice(n_layers, size=r, replace=False))
-        v = rng.random(r) + 0.05
-        v /= v.sum()
-        ids.extend(ls.tolist())
-        vals.extend(v.tolist())
-        rp.append(len(ids))
-    return np.array(rp, np.int64), np.array(ids, np.int32), np.array(vals, np.float32)
+from test_gpu_parity import random_field  # noqa: E402
 
 
 def run_cases(out):
