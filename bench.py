@@ -664,7 +664,7 @@ def run_serve(args):
     seeds = [synth.sample_seeds(cache[(sp.kind, sp.size)].n_v, sp.k, sp.seed_stream) for sp in trace]
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        with lf.Server() as srv:
+        with lf.Server(**({"chunk_steps": args.chunk_steps} if args.chunk_steps else {})) as srv:
             t0 = time.monotonic_ns()
             ids = []
             for sp, sd in zip(trace, seeds):
@@ -734,6 +734,7 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default=None,
                     help="storage type of the field values (mesh workloads; default: the workload's)")
     ap.add_argument("--serve-jobs", type=int, default=100)
+    ap.add_argument("--chunk-steps", type=int, default=0, help="serve: steps between admission rounds (0: default)")
     ap.add_argument("--cpu-sample-steps", type=int, default=200)
     ap.add_argument("--ref-sample-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
