@@ -739,6 +739,11 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.impl == "reference" and args.workload not in WORKLOADS:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times single-mesh workloads; "
+                              f"{args.workload} is a composite of them"}), flush=True)
+        return None
     if args.workload == "batch64":
         return run_batch(args)
     if args.workload == "serve":
