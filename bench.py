@@ -12,6 +12,13 @@ Under torchrun every rank runs its own jobs on its own GPU (independent jobs,
 no data-path collective: weak scaling); rank 0 prints one JSON line.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 job on the host cores.
+
+Other workloads (--workload): torus1024 and torus3300 (noisy tori of 1 M and
+10.9 M vertices), ico3, grid512_shuffled / _reordered / _morton (vertex
+numbering), grid512_general (dense coefficient matrices), batch64 (64 meshes
+in shared launches), serve (a Poisson trace through lf_server),
+grid512_lloyd (Lloyd-like rounds and the dual mesh) and dt_sweep (the time
+step study).
 """
 import argparse
 import hashlib
