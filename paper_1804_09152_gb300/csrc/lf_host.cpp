@@ -277,10 +277,6 @@ bool cotan_rows(int64_t n_v, const double* V, int64_t n_f, const int32_t* F,
   return true;
 }
 
-// The job descriptor travels inside the launch parameters, so a change to it
-// needs no upload: build_graph compares the parameters a graph was built
-// with against the current ones and rebuilds it when they differ.
-lf_status upload_job(lf_mesh) { return LF_OK; }
 
 // Launch parameters for `steps` steps of this mesh alone, starting from the
 // current buffer.
@@ -357,7 +353,7 @@ lf_status set_tile_cap(lf_mesh m, int64_t new_cap, bool keep) {
   }
   m->tile_cap = new_cap;
   m->h_job.tile_cap = static_cast<int32_t>(new_cap);
-  return upload_job(m);
+  return LF_OK;
 }
 
 // Why a step failed for good (the device error bits other than capacity).
@@ -555,9 +551,7 @@ lf_status finish_setup(lf_mesh m, const lf_params& prm) {
   // default: three entries per vertex of a tile; the band holds ~1.6 on average
   const int64_t cap = prm.initial_capacity > 0 ? (prm.initial_capacity + m->num_tiles - 1) / m->num_tiles
                                                : 3 * lf::kTile;
-  lf_status s = set_tile_cap(m, cap, false);
-  if (s == LF_OK) s = upload_job(m);
-  return s;
+  return set_tile_cap(m, cap, false);
 }
 
 // Hands a finished mesh out, or deletes a failed one keeping its message.
@@ -783,7 +777,6 @@ void drop_coefficients(lf_mesh m, bool always) {
   m->d_coef = nullptr;
   m->coef_layers = 0;
   m->h_job.cW = m->h_job.cA = m->h_job.cE = nullptr;
-  upload_job(m);
 }
 
 // Initial field (Sec. 3.2): point seeds (rings = 0) or a seed vertex with its
@@ -809,8 +802,7 @@ lf_status seed_impl(lf_mesh m, const int32_t* seeds, int32_t k, int32_t rings) {
   drop_coefficients(m, false);
   std::memset(&m->h_st, 0, sizeof(m->h_st));
   m->h_st.nnz = static_cast<unsigned long long>(m->n_v);
-  s = upload_job(m);
-  if (s == LF_OK) s = upload_status(m);
+  s = upload_status(m);
   if (s != LF_OK) return s;
   LF_CUDA(m, cudaMemcpyAsync(d_seeds, seeds, sizeof(int32_t) * k, cudaMemcpyHostToDevice, m->stream));
   if (rings == 1) {
@@ -870,7 +862,7 @@ lf_status lf_set_coefficients(lf_mesh m, int32_t n_layers, const float* W, const
   LF_CUDA(m, cudaStreamSynchronize(m->stream));
   m->d_coef = d;
   m->coef_layers = n_layers;
-  return upload_job(m);
+  return LF_OK;
 }
 
 lf_status lf_step(lf_mesh m, int32_t n_iters) {
@@ -1209,8 +1201,7 @@ lf_status lf_set_field(lf_mesh m, const int64_t* rowptr, const int32_t* layer, c
   m->h_st.nnz = static_cast<unsigned long long>(nnz);
   if (static_cast<int64_t>(m->seeds.size()) != n_layers - 1) m->seeds.clear();
   ++m->version;
-  s = upload_job(m);
-  if (s == LF_OK) s = upload_status(m);
+  s = upload_status(m);
   return s;
 }
 
