@@ -125,6 +125,29 @@ def test_server_and_batch_reject_invalid_input_without_gpu(lib):
     assert lib._lib.lf_step_batch(arr, 1, cnt) == lib.LF_ERR_INVALID      # null mesh
 
 
+def test_mesh_calls_reject_a_null_handle_without_gpu(lib):
+    # every per-mesh entry point checks its handle before any CUDA call
+    n = ctypes.c_int64()
+    seeds = np.array([0, 1], np.int32)
+    L = lib._lib
+    assert L.lf_seed(None, lib._ptr(seeds), 2) == lib.LF_ERR_INVALID
+    assert L.lf_seed_regions(None, lib._ptr(seeds), 2, 1) == lib.LF_ERR_INVALID
+    assert L.lf_set_coefficients(None, 3, None, None, None) == lib.LF_ERR_INVALID
+    assert L.lf_step(None, 1) == lib.LF_ERR_INVALID
+    assert L.lf_labels(None, None, None) == lib.LF_ERR_INVALID
+    assert L.lf_get_operator(None, None, None, None, 0, ctypes.byref(n)) == lib.LF_ERR_INVALID
+    assert L.lf_get_field(None, None, None, None, 0, ctypes.byref(n)) == lib.LF_ERR_INVALID
+    assert L.lf_lloyd(None, 1, 1, None) == lib.LF_ERR_INVALID
+    assert L.lf_extract_dual(None, None, 0, ctypes.byref(n)) == lib.LF_ERR_INVALID
+    st = lib.lf_stats_t()
+    assert L.lf_stats(None, ctypes.byref(st)) == lib.LF_ERR_INVALID
+    rp = np.array([0, 1], np.int64)
+    lay = np.array([0], np.int32)
+    val = np.array([1.0], np.float32)
+    assert L.lf_set_field(None, lib._ptr(rp), lib._ptr(lay), lib._ptr(val), 1, 2) == lib.LF_ERR_INVALID
+    L.lf_destroy_mesh(None)                    # a no-op
+
+
 def test_checked_build_compiles_and_exports_the_same_symbols():
     # the bounds-checked variant (-DLF_CHECKED) that the GPU tests compare
     # with the plain build: same sources, same entry points
