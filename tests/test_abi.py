@@ -156,3 +156,25 @@ def test_checked_build_compiles_and_exports_the_same_symbols():
     so = ctypes.CDLL(path)
     for n in declared_functions():
         assert hasattr(so, n), n
+
+
+def test_noalloc_validates_its_arguments_before_any_cuda_call(lib):
+    # the addresses below are never dereferenced: every case fails a check
+    # that comes before the first CUDA call
+    A = 1 << 20                                    # a 16-byte aligned stand-in address
+
+    def call(n_v=1000, n_layers=3, ptrs=None, tile_cap=768, params=None):
+        p = [A] * 10 if ptrs is None else ptrs
+        return lib._lib.lf_step_noalloc(None, n_v, n_layers, *p, tile_cap,
+                                        ctypes.byref(params) if params is not None else None, None, None)
+
+    assert call(ptrs=[A] * 9 + [None]) == lib.LF_ERR_INVALID
+    assert call(n_v=0) == lib.LF_ERR_INVALID
+    assert call(n_layers=1) == lib.LF_ERR_INVALID and call(n_layers=65537) == lib.LF_ERR_INVALID
+    assert call(tile_cap=128) == lib.LF_ERR_INVALID and call(tile_cap=264) == lib.LF_ERR_INVALID
+    assert call(n_v=2 ** 31 - 300, tile_cap=512) == lib.LF_ERR_CAPACITY
+    assert call(ptrs=[A, A + 4] + [A] * 8) == lib.LF_ERR_INVALID           # colval not 8-byte aligned
+    assert call(ptrs=[A] * 3 + [A + 8] + [A] * 6) == lib.LF_ERR_INVALID    # head record not 16-byte aligned
+    assert call(params=lib.lf_default_params(field_dtype="bf16")) == lib.LF_ERR_INVALID
+    assert call(params=lib.lf_default_params(dt=0.0)) == lib.LF_ERR_INVALID
+    assert "dt" in lib.lf_last_error(None)
