@@ -178,3 +178,26 @@ def test_noalloc_validates_its_arguments_before_any_cuda_call(lib):
     assert call(params=lib.lf_default_params(field_dtype="bf16")) == lib.LF_ERR_INVALID
     assert call(params=lib.lf_default_params(dt=0.0)) == lib.LF_ERR_INVALID
     assert "dt" in lib.lf_last_error(None)
+
+
+def test_the_product_never_reaches_the_oracle():
+    # the oracle is test infrastructure: the package has no path to it, and
+    # bench.py imports it only inside the function that times the CPU baseline
+    import ast
+    pkg = os.path.join(ROOT, "paper_1804_09152_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            src = open(os.path.join(pkg, name)).read()
+            assert "oracle" not in src, name
+    for name in os.listdir(os.path.join(pkg, "csrc")):
+        assert "oracle" not in open(os.path.join(pkg, "csrc", name)).read(), name
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    users = set()
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef):
+            for node in ast.walk(fn):
+                if isinstance(node, ast.Import) and any(a.name == "oracle" for a in node.names):
+                    users.add(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+    assert not any("oracle" in ast.dump(n) for n in top)
+    assert users == {"oracle_sample"}
