@@ -14,6 +14,7 @@ on Surfaces" (arXiv 1804.09152), cited in the C source:
 * ``seed_regions``    -- the same with a seed's immediate neighbours (Sec. 3.2),
 * ``lt``              -- the product L_t = Phi L^T of Algorithm 1 (Sec. 4),
 * ``step``            -- one time-iteration of Algorithm 1 (Eq. 11-13, Sec. 4),
+                         on one thread or, with the same result, on several
 * ``step_closed``     -- the same update through its closed form for the
                          class coefficients (cross-check only),
 * ``labels``          -- sharp labels, the layer of largest value (Sec. 6),
@@ -43,6 +44,12 @@ DEFAULT_PARAMS = dict(dt=5.0, mu=1.0, w_cc=0.2, w_cb=0.0, a_cc=0.04, a_cb=0.04,
                       e_cc=0.0, e_cb=0.5, e_bc=-0.5)
 _COEF_ORDER = ("dt", "mu", "w_cc", "w_cb", "a_cc", "a_cb", "e_cc", "e_cb", "e_bc")
 
+# Relative decision margin (``step(..., margins=True)``) below which a parity
+# check treats a vertex's discrete decision as a tie that rounding may flip:
+# about 800 FP32 ulps.  The tests, the smoke check and the documentation use
+# this one value.
+TIE_MARGIN = 1e-4
+
 
 def build(force=False):
     """Compile the oracle into ``oracle/_build/liblf_oracle.so``."""
@@ -50,7 +57,7 @@ def build(force=False):
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+                               "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -71,6 +78,8 @@ def _load():
         lib.orc_lt.argtypes = [i64, i32, P, P, P, P, P, P, i64, P, P, P]
         lib.orc_step.restype = i64
         lib.orc_step.argtypes = [i64, i32, P, P, P, P, P, P, P, P, P, P, i64, P, P, P, P, P]
+        lib.orc_step_threads.restype = i64
+        lib.orc_step_threads.argtypes = [i32, i64, i32, P, P, P, P, P, P, P, P, P, P, i64, P, P, P, P, P]
         lib.orc_step_closed.restype = i64
         lib.orc_step_closed.argtypes = [i64, i32, P, P, P, P, P, P, P, i64, P, P, P, P]
         lib.orc_labels.restype = ctypes.c_int
@@ -231,12 +240,14 @@ def _mat(M, n):
     return M
 
 
-def step(L, F, params=None, W=None, A=None, E=None, margins=False):
+def step(L, F, params=None, W=None, A=None, E=None, margins=False, threads=1):
     """One time-iteration of Algorithm 1 (literal triple loop).
 
     Returns ``(F_next, skeleton)`` or ``(F_next, skeleton, margins)`` where
     ``margins`` is (n_v, 3): the relative distance of the irows test and of
     the clamp to zero from flipping (see lf_oracle.c), and n_i.
+    ``threads`` other than 1 runs the same per-vertex arithmetic on that many
+    threads (0: every core; ``orc_step_threads``), with an identical result.
     """
     lib = _load()
     co = _coefs(params)
@@ -249,9 +260,10 @@ def step(L, F, params=None, W=None, A=None, E=None, margins=False):
         rp = np.zeros(F.n_v + 1, np.int64)
         ids = np.zeros(cap, np.int32)
         vals = np.zeros(cap, np.float64)
-        r = lib.orc_step(F.n_v, n, _p(L.rowptr), _p(L.col), _p(L.val),
-                         _p(F.rowptr), _p(F.ids), _p(F.vals), _p(co), _p(Wm), _p(Am), _p(Em),
-                         cap, _p(rp), _p(ids), _p(vals), _p(sk), _p(mg))
+        args = (F.n_v, n, _p(L.rowptr), _p(L.col), _p(L.val),
+                _p(F.rowptr), _p(F.ids), _p(F.vals), _p(co), _p(Wm), _p(Am), _p(Em),
+                cap, _p(rp), _p(ids), _p(vals), _p(sk), _p(mg))
+        r = lib.orc_step(*args) if threads == 1 else lib.orc_step_threads(int(threads), *args)
         if r <= -16:
             cap = int(-(r + 16)) + 16
             continue
@@ -282,11 +294,11 @@ def step_closed(L, F, params=None):
         return Field(rp, ids[:r].copy(), vals[:r].copy(), F.n_layers), int(sk[0])
 
 
-def run(L, F, n_steps, params=None, closed=False, callback=None):
+def run(L, F, n_steps, params=None, closed=False, callback=None, threads=1):
     """``n_steps`` time-iterations; returns the final field and sum of |skeleton|."""
     total = 0
     for t in range(n_steps):
-        F, sk = (step_closed(L, F, params) if closed else step(L, F, params))
+        F, sk = (step_closed(L, F, params) if closed else step(L, F, params, threads=threads))
         total += sk
         if callback is not None:
             callback(t, F)

@@ -20,10 +20,13 @@
  * Each function cites the passage it follows.  Readings of passages that are
  * silent or ambiguous are marked READING.
  */
+#define _POSIX_C_SOURCE 200809L   /* sysconf, threads */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #define ORC_OK 0
 #define ORC_ERR_INVALID (-1)
@@ -199,45 +202,72 @@ static void sort_ids(int32_t* a, int32_t n) {
 /* L_t = Phi L^T (Algorithm 1, "L_t" line; Sec. 4 "Laplacian").  Vertex-    */
 /* major: G(i, l) = sum over the stored entries (i, j) of L of L_ij F(j, l). */
 /* The pattern is structural: every layer present at some j in row i of L.   */
-/* Output rows are sorted by layer id.  Returns nnz(G), or -(needed) - 16    */
-/* when cap is too small, or a negative error code.                          */
+/* Output rows are sorted by layer id.                                        */
 /* ------------------------------------------------------------------------- */
+
+/* per-thread scratch of one row of L_t: accumulators indexed by layer */
+typedef struct { double* acc; double* aab; char* mark; int32_t* touched; } lt_scratch;
+
+static int lt_scratch_init(lt_scratch* s, int32_t n_layers) {
+  s->acc = (double*)calloc((size_t)n_layers, sizeof(double));
+  s->aab = (double*)calloc((size_t)n_layers, sizeof(double));
+  s->mark = (char*)calloc((size_t)n_layers, 1);
+  s->touched = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_layers);
+  return s->acc && s->aab && s->mark && s->touched;
+}
+
+static void lt_scratch_free(lt_scratch* s) {
+  free(s->acc); free(s->aab); free(s->mark); free(s->touched);
+}
+
+/* Row i of G: the layers touched, sorted, left in s->touched[0..return) with
+ * their sums in s->acc and the sums of the magnitudes of the products in
+ * s->aab (indexed by layer); s->mark stays set until lt_row_clear. */
+static int32_t lt_row(int64_t i, const int64_t* Lrp, const int32_t* Lcol, const double* Lval,
+                      const int64_t* Frp, const int32_t* Fid, const double* Fval, lt_scratch* s) {
+  int32_t nt = 0;
+  for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
+    int32_t j = Lcol[q];
+    double lij = Lval[q];
+    for (int64_t p = Frp[j]; p < Frp[j + 1]; ++p) {
+      int32_t l = Fid[p];
+      if (!s->mark[l]) { s->mark[l] = 1; s->touched[nt++] = l; s->acc[l] = 0.0; s->aab[l] = 0.0; }
+      s->acc[l] += lij * Fval[p];
+      s->aab[l] += fabs(lij * Fval[p]);
+    }
+  }
+  sort_ids(s->touched, nt);
+  return nt;
+}
+
+static void lt_row_clear(lt_scratch* s, int32_t nt) {
+  for (int32_t x = 0; x < nt; ++x) s->mark[s->touched[x]] = 0;
+}
+
+/* Returns nnz(G), or -(needed) - 16 when cap is too small, or a negative
+ * error code. */
 static int64_t lt_product(int64_t n_v, int32_t n_layers,
                           const int64_t* Lrp, const int32_t* Lcol, const double* Lval,
                           const int64_t* Frp, const int32_t* Fid, const double* Fval,
                           int64_t cap, int64_t* Grp, int32_t* Gid, double* Gval, double* Gabs) {
-  double* acc = (double*)calloc((size_t)n_layers, sizeof(double));
-  double* aab = (double*)calloc((size_t)n_layers, sizeof(double));
-  char* mark = (char*)calloc((size_t)n_layers, 1);
-  int32_t* touched = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_layers);
-  if (!acc || !aab || !mark || !touched) { free(acc); free(aab); free(mark); free(touched); return ORC_ERR_NOMEM; }
+  lt_scratch s;
+  if (!lt_scratch_init(&s, n_layers)) { lt_scratch_free(&s); return ORC_ERR_NOMEM; }
   int64_t o = 0;
   Grp[0] = 0;
   for (int64_t i = 0; i < n_v; ++i) {
-    int32_t nt = 0;
-    for (int64_t q = Lrp[i]; q < Lrp[i + 1]; ++q) {
-      int32_t j = Lcol[q];
-      double lij = Lval[q];
-      for (int64_t p = Frp[j]; p < Frp[j + 1]; ++p) {
-        int32_t l = Fid[p];
-        if (!mark[l]) { mark[l] = 1; touched[nt++] = l; acc[l] = 0.0; aab[l] = 0.0; }
-        acc[l] += lij * Fval[p];
-        aab[l] += fabs(lij * Fval[p]);
-      }
-    }
-    sort_ids(touched, nt);
+    int32_t nt = lt_row(i, Lrp, Lcol, Lval, Frp, Fid, Fval, &s);
     for (int32_t x = 0; x < nt; ++x) {
       if (o < cap) {
-        Gid[o] = touched[x];
-        Gval[o] = acc[touched[x]];
-        if (Gabs) Gabs[o] = aab[touched[x]];
+        Gid[o] = s.touched[x];
+        Gval[o] = s.acc[s.touched[x]];
+        if (Gabs) Gabs[o] = s.aab[s.touched[x]];
       }
       ++o;
-      mark[touched[x]] = 0;
     }
+    lt_row_clear(&s, nt);
     Grp[i + 1] = o;
   }
-  free(acc); free(aab); free(mark); free(touched);
+  lt_scratch_free(&s);
   return o > cap ? -o - 16 : o;
 }
 
@@ -246,6 +276,99 @@ int64_t orc_lt(int64_t n_v, int32_t n_layers,
                const int64_t* Frp, const int32_t* Fid, const double* Fval,
                int64_t cap, int64_t* Grp, int32_t* Gid, double* Gval) {
   return lt_product(n_v, n_layers, Lrp, Lcol, Lval, Frp, Fid, Fval, cap, Grp, Gid, Gval, NULL);
+}
+
+/* per-thread scratch of one vertex's update: the interest entries */
+typedef struct { int32_t* S; double* SF; double* SG; double* SGa; } upd_scratch;
+
+static int upd_scratch_init(upd_scratch* u, int32_t n_layers) {
+  u->S = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_layers);
+  u->SF = (double*)malloc(sizeof(double) * (size_t)n_layers);
+  u->SG = (double*)malloc(sizeof(double) * (size_t)n_layers);
+  u->SGa = (double*)malloc(sizeof(double) * (size_t)n_layers);
+  return u->S && u->SF && u->SG && u->SGa;
+}
+
+static void upd_scratch_free(upd_scratch* u) {
+  free(u->S); free(u->SF); free(u->SG); free(u->SGa);
+}
+
+/*
+ * Steps (2) and (3) below for one vertex: the sorted rows F(i, .) (nf
+ * entries) and G(i, .) (ng entries, with the magnitude sums gab) are merged;
+ * the interest entries get the explicit Euler update and the clamp.  Writes
+ * the n interest entries (ids ascending, values not yet normalised) to
+ * Hid/Hval and returns n; mg3 (nullable) receives the margins described at
+ * orc_step.
+ */
+static int32_t vertex_update(const orc_coefs* cp, int32_t n_layers, const double* Wm, const double* Am,
+                             const double* Em, const int32_t* fid, const double* fval, int64_t nf,
+                             const int32_t* gid, const double* gval, const double* gab, int64_t ng,
+                             upd_scratch* u, int32_t* Hid, double* Hval, double* mg3) {
+  const orc_coefs c = *cp;
+  int32_t* S = u->S;
+  double* SF = u->SF;
+  double* SG = u->SG;
+  double* SGa = u->SGa;
+  /* merge the sorted patterns of F(i, .) and G(i, .) */
+  int64_t pf = 0, pg = 0;
+  int32_t n = 0;
+  double mG = HUGE_VAL, mC = HUGE_VAL;
+  while (pf < nf || pg < ng) {
+    int32_t lf = pf < nf ? fid[pf] : INT32_MAX;
+    int32_t lg = pg < ng ? gid[pg] : INT32_MAX;
+    int32_t l = lf < lg ? lf : lg;
+    double fv = (lf == l) ? fval[pf] : 0.0;
+    double gv = (lg == l) ? gval[pg] : 0.0;
+    double ga = (lg == l) ? gab[pg] : 0.0;
+    if (lf == l) ++pf;
+    if (lg == l) ++pg;
+    if (fv == 0.0 && ga > 0.0 && fabs(gv) / ga < mG) mG = fabs(gv) / ga;
+    if (fv > 0.0 || (fv == 0.0 && gv > 0.0)) {
+      S[n] = l; SF[n] = fv; SG[n] = gv; SGa[n] = ga; ++n;
+    }
+  }
+  for (int32_t jj = 0; jj < n; ++jj) {
+    int32_t j = S[jj];
+    double d = 0.0, dabs = 0.0;
+    for (int32_t kk = 0; kk < n; ++kk) {
+      int32_t kx = S[kk];
+      double sum = 0.0, sabs = 0.0;
+      for (int32_t ll = 0; ll < n; ++ll) {
+        int32_t l = S[ll];
+        double ca = 0.5 * (coef_sym(Am, c.a_cc, c.a_cb, n_layers, j, l) - coef_sym(Am, c.a_cc, c.a_cb, n_layers, kx, l));
+        double tw = (coef_sym(Wm, c.w_cc, c.w_cb, n_layers, j, l) - coef_sym(Wm, c.w_cc, c.w_cb, n_layers, kx, l)) * SF[ll];
+        sum += ca * SG[ll] + tw;
+        sabs += fabs(ca) * SGa[ll] + fabs(tw);
+      }
+      double te = coef_e(Em, &c, n_layers, j, kx) * sqrt(SF[jj] * SF[kk]);
+      d += -(c.mu / n) * (sum - te);
+      dabs += (c.mu / n) * (sabs + fabs(te));
+    }
+    double v = SF[jj] + d * c.dt;
+    double vscale = fabs(SF[jj]) + c.dt * dabs;
+    if (vscale > 0.0 && fabs(v) / vscale < mC) mC = fabs(v) / vscale;
+    if (v > 1.0) v = 1.0;
+    if (v <= 0.0) v = 0.0;
+    Hid[jj] = j;
+    Hval[jj] = v;
+  }
+  if (mg3) {
+    mg3[0] = mG;
+    mg3[1] = mC;
+    mg3[2] = (double)n;
+  }
+  return n;
+}
+
+/* Step (4) for one vertex: divide its n entries by their sum.  Returns 0, or
+ * ORC_ERR_ZERO_SUM when the sum is not positive. */
+static int normalise_row(double* Hval, int64_t n) {
+  double s = 0.0;
+  for (int64_t p = 0; p < n; ++p) s += Hval[p];
+  if (!(s > 0.0)) return ORC_ERR_ZERO_SUM;
+  for (int64_t p = 0; p < n; ++p) Hval[p] = Hval[p] / s;
+  return ORC_OK;
 }
 
 /*
@@ -294,11 +417,9 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
   int64_t* Hrp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_v + 1));
   int32_t* Hid = NULL;
   double* Hval = NULL;
-  int32_t* S = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_layers);
-  double* SF = (double*)malloc(sizeof(double) * (size_t)n_layers);
-  double* SG = (double*)malloc(sizeof(double) * (size_t)n_layers);
-  double* SGa = (double*)malloc(sizeof(double) * (size_t)n_layers);
-  if (!Grp || !Hrp || !S || !SF || !SG || !SGa) { ret = ORC_ERR_NOMEM; goto done; }
+  upd_scratch u;
+  int uok = upd_scratch_init(&u, n_layers);
+  if (!Grp || !Hrp || !uok) { ret = ORC_ERR_NOMEM; goto done; }
 
   /* (1) L_t */
   for (;;) {
@@ -321,65 +442,17 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
   int64_t skel = 0;
   Hrp[0] = 0;
   for (int64_t i = 0; i < n_v; ++i) {
-    /* merge the sorted patterns of F(i, .) and G(i, .) */
-    int64_t pf = Frp[i], pg = Grp[i];
-    int32_t n = 0;
-    double mG = HUGE_VAL, mC = HUGE_VAL;
-    while (pf < Frp[i + 1] || pg < Grp[i + 1]) {
-      int32_t lf = pf < Frp[i + 1] ? Fid[pf] : INT32_MAX;
-      int32_t lg = pg < Grp[i + 1] ? Gid[pg] : INT32_MAX;
-      int32_t l = lf < lg ? lf : lg;
-      double fv = (lf == l) ? Fval[pf] : 0.0;
-      double gv = (lg == l) ? Gval[pg] : 0.0;
-      double ga = (lg == l) ? Gab[pg] : 0.0;
-      if (lf == l) ++pf;
-      if (lg == l) ++pg;
-      if (fv == 0.0 && ga > 0.0 && fabs(gv) / ga < mG) mG = fabs(gv) / ga;
-      if (fv > 0.0 || (fv == 0.0 && gv > 0.0)) {
-        S[n] = l; SF[n] = fv; SG[n] = gv; SGa[n] = ga; ++n;
-      }
-    }
+    int32_t n = vertex_update(&c, n_layers, Wm, Am, Em, Fid + Frp[i], Fval + Frp[i], Frp[i + 1] - Frp[i],
+                              Gid + Grp[i], Gval + Grp[i], Gab + Grp[i], Grp[i + 1] - Grp[i], &u,
+                              Hid + Hrp[i], Hval + Hrp[i], margins ? margins + 3 * i : NULL);
     skel += n;
     Hrp[i + 1] = Hrp[i] + n;
-    for (int32_t jj = 0; jj < n; ++jj) {
-      int32_t j = S[jj];
-      double d = 0.0, dabs = 0.0;
-      for (int32_t kk = 0; kk < n; ++kk) {
-        int32_t kx = S[kk];
-        double sum = 0.0, sabs = 0.0;
-        for (int32_t ll = 0; ll < n; ++ll) {
-          int32_t l = S[ll];
-          double ca = 0.5 * (coef_sym(Am, c.a_cc, c.a_cb, n_layers, j, l) - coef_sym(Am, c.a_cc, c.a_cb, n_layers, kx, l));
-          double tw = (coef_sym(Wm, c.w_cc, c.w_cb, n_layers, j, l) - coef_sym(Wm, c.w_cc, c.w_cb, n_layers, kx, l)) * SF[ll];
-          sum += ca * SG[ll] + tw;
-          sabs += fabs(ca) * SGa[ll] + fabs(tw);
-        }
-        double te = coef_e(Em, &c, n_layers, j, kx) * sqrt(SF[jj] * SF[kk]);
-        d += -(c.mu / n) * (sum - te);
-        dabs += (c.mu / n) * (sabs + fabs(te));
-      }
-      double v = SF[jj] + d * c.dt;
-      double vscale = fabs(SF[jj]) + c.dt * dabs;
-      if (vscale > 0.0 && fabs(v) / vscale < mC) mC = fabs(v) / vscale;
-      if (v > 1.0) v = 1.0;
-      if (v <= 0.0) v = 0.0;
-      Hid[Hrp[i] + jj] = j;
-      Hval[Hrp[i] + jj] = v;
-    }
-    if (margins) {
-      margins[3 * i] = mG;
-      margins[3 * i + 1] = mC;
-      margins[3 * i + 2] = (double)n;
-    }
   }
   if (skeleton) *skeleton = skel;
 
   /* (4) normalise each vertex by the sum of its entries */
   for (int64_t i = 0; i < n_v; ++i) {
-    double s = 0.0;
-    for (int64_t p = Hrp[i]; p < Hrp[i + 1]; ++p) s += Hval[p];
-    if (!(s > 0.0)) { ret = ORC_ERR_ZERO_SUM; goto done; }
-    for (int64_t p = Hrp[i]; p < Hrp[i + 1]; ++p) Hval[p] = Hval[p] / s;
+    if (normalise_row(Hval + Hrp[i], Hrp[i + 1] - Hrp[i]) != ORC_OK) { ret = ORC_ERR_ZERO_SUM; goto done; }
   }
 
   /* (5) compaction: keep the nonzero entries */
@@ -400,7 +473,145 @@ int64_t orc_step(int64_t n_v, int32_t n_layers,
 
 done:
   free(Grp); free(Gid); free(Gval); free(Gab); free(Hrp); free(Hid); free(Hval);
-  free(S); free(SF); free(SG); free(SGa);
+  upd_scratch_free(&u);
+  return ret;
+}
+
+/*
+ * The same time-iteration computed by several threads (the timed CPU
+ * baseline): each thread takes a contiguous range of vertices and runs
+ * steps (1)-(5) for one vertex at a time with the helpers of orc_step, so
+ * every vertex gets the same operations in the same order and the result is
+ * identical to orc_step's.  Every vertex's work reads only the input, so the
+ * threads need no locks; each keeps its output rows in a buffer of its own,
+ * and a prefix sum of the per-thread counts places them in the output.
+ * n_threads <= 0 uses every online core.  Same outputs and return codes as
+ * orc_step.
+ */
+typedef struct {
+  int64_t lo, hi;
+  int32_t n_layers;
+  const int64_t *Lrp, *Frp;
+  const int32_t *Lcol, *Fid;
+  const double *Lval, *Fval, *Wm, *Am, *Em;
+  const orc_coefs* c;
+  double* margins;
+  int64_t* counts;       /* per vertex: output entries */
+  int32_t* oid;          /* this thread's output entries */
+  double* oval;
+  int64_t n_out, cap, skel;
+  int err;
+} mt_task;
+
+static void* mt_worker(void* arg) {
+  mt_task* t = (mt_task*)arg;
+  lt_scratch s;
+  upd_scratch u;
+  int ok = lt_scratch_init(&s, t->n_layers) & upd_scratch_init(&u, t->n_layers);
+  int32_t* gid = (int32_t*)malloc(sizeof(int32_t) * (size_t)t->n_layers);
+  double* gval = (double*)malloc(sizeof(double) * (size_t)t->n_layers);
+  double* gab = (double*)malloc(sizeof(double) * (size_t)t->n_layers);
+  int32_t* hid = (int32_t*)malloc(sizeof(int32_t) * (size_t)t->n_layers);
+  double* hval = (double*)malloc(sizeof(double) * (size_t)t->n_layers);
+  t->cap = 1024;
+  t->oid = (int32_t*)malloc(sizeof(int32_t) * (size_t)t->cap);
+  t->oval = (double*)malloc(sizeof(double) * (size_t)t->cap);
+  t->n_out = 0;
+  t->skel = 0;
+  t->err = ORC_OK;
+  if (!ok || !gid || !gval || !gab || !hid || !hval || !t->oid || !t->oval) { t->err = ORC_ERR_NOMEM; goto out; }
+  for (int64_t i = t->lo; i < t->hi; ++i) {
+    int32_t ng = lt_row(i, t->Lrp, t->Lcol, t->Lval, t->Frp, t->Fid, t->Fval, &s);
+    for (int32_t x = 0; x < ng; ++x) {
+      gid[x] = s.touched[x];
+      gval[x] = s.acc[s.touched[x]];
+      gab[x] = s.aab[s.touched[x]];
+    }
+    lt_row_clear(&s, ng);
+    int32_t n = vertex_update(t->c, t->n_layers, t->Wm, t->Am, t->Em, t->Fid + t->Frp[i], t->Fval + t->Frp[i],
+                              t->Frp[i + 1] - t->Frp[i], gid, gval, gab, ng, &u, hid, hval,
+                              t->margins ? t->margins + 3 * i : NULL);
+    t->skel += n;
+    if (normalise_row(hval, n) != ORC_OK) { t->err = ORC_ERR_ZERO_SUM; goto out; }
+    if (t->n_out + n > t->cap) {
+      while (t->n_out + n > t->cap) t->cap *= 2;
+      int32_t* a = (int32_t*)realloc(t->oid, sizeof(int32_t) * (size_t)t->cap);
+      if (a) t->oid = a;
+      double* b = (double*)realloc(t->oval, sizeof(double) * (size_t)t->cap);
+      if (b) t->oval = b;
+      if (!a || !b) { t->err = ORC_ERR_NOMEM; goto out; }
+    }
+    int64_t kept = 0;
+    for (int32_t p = 0; p < n; ++p) {
+      if (hval[p] != 0.0) { t->oid[t->n_out + kept] = hid[p]; t->oval[t->n_out + kept] = hval[p]; ++kept; }
+    }
+    t->n_out += kept;
+    t->counts[i] = kept;
+  }
+out:
+  lt_scratch_free(&s);
+  upd_scratch_free(&u);
+  free(gid); free(gval); free(gab); free(hid); free(hval);
+  return NULL;
+}
+
+int64_t orc_step_threads(int32_t n_threads, int64_t n_v, int32_t n_layers,
+                         const int64_t* Lrp, const int32_t* Lcol, const double* Lval,
+                         const int64_t* Frp, const int32_t* Fid, const double* Fval,
+                         const double* coefs, const double* Wm, const double* Am, const double* Em,
+                         int64_t out_cap, int64_t* Orp, int32_t* Oid, double* Oval,
+                         int64_t* skeleton, double* margins) {
+  const orc_coefs c = unpack(coefs);
+  if (n_threads <= 0) {
+    long nc = sysconf(_SC_NPROCESSORS_ONLN);
+    n_threads = nc > 0 ? (int32_t)nc : 1;
+  }
+  if (n_threads > n_v) n_threads = n_v > 0 ? (int32_t)n_v : 1;
+  mt_task* tasks = (mt_task*)calloc((size_t)n_threads, sizeof(mt_task));
+  pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+  char* running = (char*)calloc((size_t)n_threads, 1);
+  int64_t* counts = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_v > 0 ? n_v : 1));
+  if (!tasks || !th || !running || !counts) { free(tasks); free(th); free(running); free(counts); return ORC_ERR_NOMEM; }
+  for (int32_t k = 0; k < n_threads; ++k) {
+    mt_task* t = &tasks[k];
+    t->lo = n_v * k / n_threads;
+    t->hi = n_v * (k + 1) / n_threads;
+    t->n_layers = n_layers;
+    t->Lrp = Lrp; t->Lcol = Lcol; t->Lval = Lval;
+    t->Frp = Frp; t->Fid = Fid; t->Fval = Fval;
+    t->Wm = Wm; t->Am = Am; t->Em = Em;
+    t->c = &c;
+    t->margins = margins;
+    t->counts = counts;
+    t->err = ORC_ERR_NOMEM;
+    if (k > 0) running[k] = pthread_create(&th[k], NULL, mt_worker, t) == 0;
+  }
+  for (int32_t k = 0; k < n_threads; ++k)
+    if (!running[k]) mt_worker(&tasks[k]);     /* the calling thread, and any thread not to be had */
+  for (int32_t k = 1; k < n_threads; ++k)
+    if (running[k]) pthread_join(th[k], NULL);
+  int64_t ret = 0, nnz = 0, skel = 0;
+  for (int32_t k = 0; k < n_threads; ++k) {
+    if (tasks[k].err != ORC_OK && ret == 0) ret = tasks[k].err;
+    nnz += tasks[k].n_out;
+    skel += tasks[k].skel;
+  }
+  if (ret == 0 && nnz > out_cap) ret = -nnz - 16;
+  if (ret == 0) {
+    /* prefix sum of the per-thread counts: each thread's rows in place */
+    int64_t o = 0;
+    for (int32_t k = 0; k < n_threads; ++k) {
+      memcpy(Oid + o, tasks[k].oid, sizeof(int32_t) * (size_t)tasks[k].n_out);
+      memcpy(Oval + o, tasks[k].oval, sizeof(double) * (size_t)tasks[k].n_out);
+      o += tasks[k].n_out;
+    }
+    Orp[0] = 0;
+    for (int64_t i = 0; i < n_v; ++i) Orp[i + 1] = Orp[i] + counts[i];
+    if (skeleton) *skeleton = skel;
+    ret = nnz;
+  }
+  for (int32_t k = 0; k < n_threads; ++k) { free(tasks[k].oid); free(tasks[k].oval); }
+  free(tasks); free(th); free(running); free(counts);
   return ret;
 }
 

@@ -14,7 +14,7 @@ import pytest
 
 import synth
 from oracle import dual, tessellation as tz
-from parity_util import to_f32
+from parity_util import lloyd_differences_explained, to_f32
 from test_gpu_parity import check_results, single_step_parity
 
 pytestmark = pytest.mark.gpu
@@ -73,9 +73,8 @@ def test_grid512_lloyd_update_and_dual_full_size(lf, oracle_mod):
     # seeds: exact except cells whose decision is a tie (and cells that meet
     # a tie cell in a conflict)
     ties = np.flatnonzero(marg < TIE)
-    tie_vertices = set(got[ties].tolist()) | set(want[ties].tolist())
-    for c in np.flatnonzero(got != want):
-        assert c in ties or got[c] == seeds[c] or want[c] == seeds[c] or want[c] in tie_vertices, c
+    left = lloyd_differences_explained(got, want, seeds, cand, ties)
+    assert not left, (left, got[left], want[left], cand[left])
     assert len(set(got.tolist())) == k and (got != seeds).sum() > k // 2
     # dual mesh: the same triangles, orientation included
     assert dmargin > 1e-12

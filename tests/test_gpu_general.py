@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synth
-from parity_util import FIELD_TOL, ambiguous_rows, compare, field_from_lib, to_f32
+from parity_util import ambiguous_rows, check_compare, compare, field_from_lib, to_f32
 from test_gpu_parity import check_results, random_field
 
 pytestmark = pytest.mark.gpu
@@ -115,7 +115,7 @@ def test_general_matrices_on_large_layer_unions(lf, oracle_mod, per_row, n_layer
     Fin = oracle_mod.Field(rp, ids, vals.astype(np.float64), n_layers)
     Fo, _, mg = oracle_mod.step(L, Fin, W=W, A=A, E=E, margins=True)
     r = compare(Fo, Fg, ambiguous_rows(mg), oracle_mod)
-    assert r["unexplained"] == 0 and r["max_err"] <= FIELD_TOL, r
+    check_compare(r)
 
 
 def test_one_matrix_keeps_the_class_rule_for_the_others(lf, oracle_mod):
@@ -136,7 +136,7 @@ def test_one_matrix_keeps_the_class_rule_for_the_others(lf, oracle_mod):
         mesh.step(1)
         Fg = field_from_lib(*mesh.get_field(), k + 1, oracle_mod)
     r = compare(Fo, Fg, ambiguous_rows(mg), oracle_mod)
-    assert r["unexplained"] == 0 and r["max_err"] <= FIELD_TOL, r
+    check_compare(r)
 
 
 def run_alone(lf, m, seeds, steps, mats=None):

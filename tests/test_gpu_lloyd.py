@@ -6,14 +6,16 @@ give the same new seeds.  A cell whose oracle decision is within rounding of
 going the other way (hit on a face edge, two hits or two vertices at nearly
 the same distance) is a tie; the GPU's per-cell sums are FP64 atomics in
 varying order, so such a cell may differ, and so may cells it meets in a
-conflict.  Longer runs are checked for what holds at any size.
+conflict over its candidate vertex (and so on along the chain of conflicts);
+every other cell must match.  Longer runs are checked for what holds at any
+size.
 """
 import numpy as np
 import pytest
 
 import synth
 from oracle import tessellation as tz
-from parity_util import to_f32
+from parity_util import lloyd_differences_explained, to_f32
 
 pytestmark = pytest.mark.gpu
 
@@ -60,10 +62,10 @@ def test_one_update_matches_the_oracle(lf, oracle_mod, name):
     if ties.size == 0:
         assert bad.size == 0, (bad, got[bad], want[bad])
     else:
-        # a differing cell is a tie, or lost a conflict to a vertex a tie cell took
-        tie_vertices = set(got[ties].tolist()) | set(want[ties].tolist())
-        for c in bad:
-            assert c in ties or got[c] == seeds[c] or want[c] == seeds[c] or want[c] in tie_vertices, c
+        # a differing cell is a tie, or met a tie cell (or a cell explained
+        # so) in a conflict over its candidate
+        left = lloyd_differences_explained(got, want, seeds, cand, ties)
+        assert not left, (left, got[left], want[left], cand[left])
     assert (got != seeds).any()                                # the update moves seeds
 
 

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from parity_util import FIELD_TOL, ambiguous_rows, compare, field_from_lib, to_f32
+from parity_util import FIELD_TOL, ambiguous_rows, check_compare, compare, field_from_lib, to_f32
 
 pytestmark = pytest.mark.gpu
 
@@ -57,15 +57,19 @@ def single_step_parity(lf, oracle, m, seeds, checks, params=None):
     return out
 
 
-def check_results(res, max_disagree_frac=0.05):
+def check_results(res):
     """Every row agrees within FIELD_TOL with an identical pattern, except
-    rows whose decisions are ties; those stay a small fraction."""
+    rows whose decisions are ties; those may differ in entries of at most
+    FIELD_TOL, and the ties whose flip moved a value further stay within the
+    stated fraction (parity_util.check_compare).  The skeleton sizes differ
+    only through such rows."""
     for r in res:
-        assert r["unexplained"] == 0, r
-        assert r["max_err"] <= FIELD_TOL, r
-        assert r["pattern_mismatch"] == 0, r
-        assert r["disagreeing_rows"] <= max_disagree_frac * r["rows"] + 2, r
+        check_compare(r)
         assert r["sk_diff"] <= 16 * r["disagreeing_rows"], r
+    worst = max(res, key=lambda r: r["value_rows"] / r["rows"])
+    print(f"parity: {len(res)} steps, tie rows <= {max(r['tie_rows'] / r['rows'] for r in res):.2%}, "
+          f"value-disagreeing rows <= {worst['value_rows'] / worst['rows']:.3%} "
+          f"(t={worst['t']}), max error off ties {max(r['max_err'] for r in res):.2e}")
 
 
 @pytest.mark.parametrize("name", list(MESHES))
@@ -203,7 +207,7 @@ def test_large_layer_unions_match(lf, oracle_mod, per_row, n_layers):
     Fo, _, mg = oracle_mod.step(L, Fin, margins=True)
     Fg = field_from_lib(*mesh.get_field(), n_layers, oracle_mod)
     r = compare(Fo, Fg, ambiguous_rows(mg), oracle_mod)
-    assert r["unexplained"] == 0 and r["max_err"] <= FIELD_TOL, r
+    check_compare(r)
     mesh.close()
 
 

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synth
-from parity_util import ambiguous_rows, compare, field_from_lib, to_f32
+from parity_util import ambiguous_rows, check_compare, compare, field_from_lib, to_f32
 
 pytestmark = pytest.mark.gpu
 
@@ -40,8 +40,7 @@ def test_region_seeds_and_steps_match_the_oracle(lf, oracle_mod, name, fac, k, s
             mesh.step(1)
             skg = mesh.stats()["skeleton_total"] - sk0
             r = compare(Fo, field_from_lib(*mesh.get_field(), F.n_layers, oracle_mod), ambiguous_rows(mg), oracle_mod)
-            assert r["unexplained"] == 0 and r["pattern_mismatch"] == 0, r
-            assert r["disagreeing_rows"] <= 0.05 * r["rows"] + 2, r
+            check_compare(r)
             assert abs(int(skg) - int(sko)) <= 16 * r["disagreeing_rows"], (t, skg, sko)
             F, _ = oracle_mod.step(L, F, {})
 

@@ -392,6 +392,172 @@ def test_single_layer_is_fixed_point(oracle_mod):
 
 
 # ----------------------------------------------------------------------------
+# decision margins (the tie classifier of the GPU parity tests)
+# ----------------------------------------------------------------------------
+#
+# orc_step reports per vertex how far its two discrete decisions are from
+# flipping: [0] the irows test on an entry with F = 0 (|G| over the sum of the
+# magnitudes of the products that make G), [1] the clamp at zero (|F + d dt|
+# over |F| plus dt times the sum of the magnitudes of the terms of d, each G
+# counted by its magnitude sum).  The parity tests exclude a row as a tie
+# when either is below the tie threshold, so both are pinned here by hand.
+
+def three_vertex_cancellation_operator():
+    """L = [[0, .5, -.5], [.5, -.5, 0], [-.5, 0, .5]]: rows sum to zero and
+    vertex 0 sees its two neighbours with opposite weights (a negative
+    cotangent weight, as on jittered meshes)."""
+    return np.array([[0.0, 0.5, -0.5], [0.5, -0.5, 0.0], [-0.5, 0.0, 0.5]])
+
+
+@pytest.mark.parametrize("x1,x2,want", [(0.75, 0.25, 0.5), (0.25, 0.75, 0.5), (0.9, 0.1, 0.8), (0.5, 0.5, 0.0)])
+def test_irows_margin_by_hand(oracle_mod, x1, x2, want):
+    """Vertex 0 holds the base layer only; vertices 1 and 2 hold cell 0 at x1
+    and x2 (the base layer at the rest).  Cell 0 is absent at vertex 0, so its
+    irows test is on G(0, cell) = .5 x1 - .5 x2, whose magnitude sum is
+    .5 x1 + .5 x2: margin |x1 - x2| / (x1 + x2).  With x1 = x2 the two
+    products cancel exactly: margin 0, and the cell stays out of irows.
+    Vertices 1 and 2 hold every layer of their neighbourhood: no such entry."""
+    L = oracle_mod.operator_from_dense(three_vertex_cancellation_operator())
+    F = make_field(oracle_mod, [{1: 1.0}, {0: x1, 1: 1 - x1}, {0: x2, 1: 1 - x2}], 2)
+    _, _, mg = oracle_mod.step(L, F, margins=True)
+    assert abs(mg[0, 0] - want) < 1e-15
+    assert mg[1, 0] == math.inf and mg[2, 0] == math.inf
+    assert mg[0, 2] == (2 if x1 > x2 else 1)          # the cell enters irows iff G > 0
+
+
+def test_clamp_margin_with_cancelling_g_by_hand(oracle_mod):
+    """The case above with x1 = .75, x2 = .25 and the default parameters
+    (a_cb = .04, w_cb = 0, e_cb = -e_bc = .5, mu = 1, dt = 5).
+
+    At vertex 0: G_cell = .25 (magnitude sum .5), G_base = .125 - .375 = -.25
+    (magnitude sum .5); irows = {cell, base}, n = 2.
+      cell: sum_{cell,base} = 1/2 (0 - a_cb) G_cell + 1/2 (a_cb - 0) G_base = -.01,
+            its magnitude sum .02 (.02 * .5 twice), e term 0 (F_cell = 0):
+            d = .005, d dt = .025, scale 0 + 5 * (.02 / 2) = .05 -> margin .5;
+      base: sum = +.01, d = -.005, value .975, scale 1 + .05 -> margin .975 / 1.05.
+    Counting G by |G| (.25) instead of its magnitude sum (.5) would give 1.
+    """
+    L = oracle_mod.operator_from_dense(three_vertex_cancellation_operator())
+    F = make_field(oracle_mod, [{1: 1.0}, {0: 0.75, 1: 0.25}, {0: 0.25, 1: 0.75}], 2)
+    out, _, mg = oracle_mod.step(L, F, margins=True)
+    assert abs(mg[0, 1] - 0.5) < 1e-14
+    got = row_dict(out, 0)
+    assert abs(got[0] - 0.025) < 1e-14 and abs(got[1] - 0.975) < 1e-14
+
+
+def test_two_vertex_front_margins_by_hand(oracle_mod):
+    """Operator [[-1, 1], [1, -1]], vertex 0 = {cell 1.0}, vertex 1 = {base 1.0},
+    default parameters.  Vertex 1: the cell enters with G = 1 from one product
+    (margin 1); irows = {cell, base}; cell: sum = -.02 - .02 = -.04 over a
+    magnitude sum .04, d = .02, value .1 over scale 5 * .02 = .1 -> 1;
+    base: value .9 over scale 1.1 -> 9/11.  Vertex 0 is the mirror image."""
+    L = oracle_mod.operator_from_dense(np.array([[-1.0, 1.0], [1.0, -1.0]]))
+    F = make_field(oracle_mod, [{0: 1.0}, {1: 1.0}], 2)
+    _, _, mg = oracle_mod.step(L, F, margins=True)
+    for i in range(2):
+        assert abs(mg[i, 0] - 1.0) < 1e-15
+        assert abs(mg[i, 1] - 9.0 / 11.0) < 1e-14
+        assert mg[i, 2] == 2
+
+
+@pytest.mark.parametrize("p_,want", [(0.6, 1.0 / 3.0), (0.3, 0.125), (0.75, 0.0), (0.25, 0.0)])
+def test_isolated_two_cells_clamp_margin_by_hand(oracle_mod, p_, want):
+    """One vertex, G = 0, cells at p and 1 - p, default parameters (w_cc = .2,
+    e_cc = 0, mu = 1, dt = 5).  For cell 0 the double sum is w (1 - 2p) with
+    magnitude sum w, so d = -(w/2)(1 - 2p) and the scale is p + dt w / 2;
+    cell 1 likewise with p -> 1 - p.
+      p = .6:  cell 0 .7 / 1.1, cell 1 .3 / .9 = 1/3;
+      p = .3:  cell 0 (.3 - .2) / (.3 + .5) = .125, cell 1 .9 / 1.2;
+      p = .75: cell 1 lands exactly on the clamp, .25 - .25 = 0 (p = .25: cell 0)."""
+    L = oracle_mod.operator_from_dense(np.zeros((1, 1)))
+    F = make_field(oracle_mod, [{0: p_, 1: 1 - p_}], 3)
+    _, _, mg = oracle_mod.step(L, F, margins=True)
+    assert abs(mg[0, 1] - want) < 1e-14
+    assert mg[0, 0] == math.inf                       # no entry with F = 0
+    assert mg[0, 2] == 2
+
+
+def test_isolated_cell_and_base_clamp_margin_by_hand(oracle_mod):
+    """One vertex, G = 0, cell 0 at .6 and the base at .4, default parameters.
+    Only the band terms act (w_cb = 0): cell d = +(1/2) e_cb s, base
+    d = -(1/2) e_cb s with s = sqrt(.24); the cell's margin is 1 (one term),
+    the base's |.4 - 1.25 s| / (.4 + 1.25 s)."""
+    L = oracle_mod.operator_from_dense(np.zeros((1, 1)))
+    F = make_field(oracle_mod, [{0: 0.6, 1: 0.4}], 2)
+    _, _, mg = oracle_mod.step(L, F, margins=True)
+    s = math.sqrt(0.24)
+    assert abs(mg[0, 1] - (1.25 * s - 0.4) / (0.4 + 1.25 * s)) < 1e-14
+
+
+def brute_force_margins(Ld, D, params, base):
+    """Margins of one step from the dense operator and field, written from the
+    definitions: every layer of the closed neighbourhood, Algorithm 1's double
+    sum per interest entry with every term replaced by its magnitude (G by the
+    magnitude sum of its products) for the scale."""
+    p = params
+    n_v, K = D.shape
+
+    def coef(cc, cb, j, l):
+        if j == l:
+            return 0.0
+        return cb if (j == base or l == base) else cc
+
+    def ecoef(j, k):
+        if j == k:
+            return 0.0
+        if j == base:
+            return p["e_bc"]
+        return p["e_cb"] if k == base else p["e_cc"]
+
+    G = Ld @ D
+    Ga = np.abs(Ld) @ D
+    struct = (np.abs(Ld) > 0).astype(int) @ (D > 0).astype(int) > 0
+    out = np.full((n_v, 3), math.inf)
+    for i in range(n_v):
+        cand = [l for l in range(K) if D[i, l] == 0 and struct[i, l] and Ga[i, l] > 0]
+        if cand:
+            out[i, 0] = min(abs(G[i, l]) / Ga[i, l] for l in cand)
+        S = [l for l in range(K) if D[i, l] > 0 or (D[i, l] == 0 and struct[i, l] and G[i, l] > 0)]
+        n = len(S)
+        out[i, 2] = n
+        for j in S:
+            d = dabs = 0.0
+            for k in S:
+                s = sa = 0.0
+                for l in S:
+                    ca = 0.5 * (coef(p["a_cc"], p["a_cb"], j, l) - coef(p["a_cc"], p["a_cb"], k, l))
+                    tw = (coef(p["w_cc"], p["w_cb"], j, l) - coef(p["w_cc"], p["w_cb"], k, l)) * D[i, l]
+                    s += ca * G[i, l] + tw
+                    sa += abs(ca) * Ga[i, l] + abs(tw)
+                te = ecoef(j, k) * math.sqrt(D[i, j] * D[i, k])
+                d += -(p["mu"] / n) * (s - te)
+                dabs += (p["mu"] / n) * (sa + abs(te))
+            v = D[i, j] + d * p["dt"]
+            scale = D[i, j] + p["dt"] * dabs
+            if scale > 0:
+                out[i, 1] = min(out[i, 1], abs(v) / scale)
+    return out
+
+
+@pytest.mark.parametrize("params", PARAM_SETS)
+@pytest.mark.parametrize("mesh", ["grid5", "torus5"])
+def test_margins_match_brute_force(oracle_mod, params, mesh):
+    m = {"grid5": lambda: synth.planar_grid(5, jitter=0.2, seed=2), "torus5": lambda: synth.noisy_torus(5)}[mesh]()
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    rng = np.random.default_rng(11)
+    F, D = random_field(oracle_mod, m.n_v, 6, rng, density=0.35)
+    p = dict(oracle_mod.DEFAULT_PARAMS)
+    p.update(params)
+    _, _, mg = oracle_mod.step(L, F, params, margins=True)
+    want = brute_force_margins(L.dense(), D, p, base=5)
+    assert np.array_equal(mg[:, 2], want[:, 2])
+    for c in (0, 1):
+        fin = np.isfinite(want[:, c])
+        assert np.array_equal(fin, np.isfinite(mg[:, c]))
+        assert np.abs(mg[fin, c] - want[fin, c]).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------
 # literal triple loop vs closed form
 # ----------------------------------------------------------------------------
 
@@ -524,3 +690,42 @@ def test_partition_insensitive_to_time_step(oracle_mod):
     F5, _ = oracle_mod.run(L, oracle_mod.seed(m.n_v, seeds), 120, dict(dt=5.0))
     F1, _ = oracle_mod.run(L, oracle_mod.seed(m.n_v, seeds), 400, dict(dt=1.0))
     assert np.mean(oracle_mod.labels(F5) == oracle_mod.labels(F1)) > 0.95
+
+
+# ----------------------------------------------------------------------------
+# the threaded step (the timed CPU baseline) is the literal step
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("threads", [2, 3, 7, 0])
+@pytest.mark.parametrize("params", PARAM_SETS[:2])
+def test_threaded_step_is_identical(oracle_mod, threads, params):
+    """Several threads over vertex ranges give the single-thread step's
+    arrays bit for bit, margins and skeleton size included, along a
+    trajectory with growing and shrinking rows."""
+    m = synth.noisy_torus(20)
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    F = oracle_mod.seed(m.n_v, synth.sample_seeds(m.n_v, 24, 2))
+    for _ in range(25):
+        a, ska, ma = oracle_mod.step(L, F, params, margins=True)
+        b, skb, mb = oracle_mod.step(L, F, params, margins=True, threads=threads)
+        assert ska == skb
+        for x, y in ((a.rowptr, b.rowptr), (a.ids, b.ids), (a.vals, b.vals), (ma, mb)):
+            assert np.array_equal(x, y)
+        F = a
+
+
+def test_threaded_step_with_matrices_and_tiny_meshes(oracle_mod):
+    rng = np.random.default_rng(5)
+    m = synth.planar_grid(7, jitter=0.2, seed=2)
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    F, _ = random_field(oracle_mod, m.n_v, 5, rng, density=0.4)
+    W, A, E = (rng.random((5, 5)) * 0.3 for _ in range(3))
+    a, ska = oracle_mod.step(L, F, W=W, A=A, E=E)
+    b, skb = oracle_mod.step(L, F, W=W, A=A, E=E, threads=4)
+    assert ska == skb and np.array_equal(a.vals, b.vals) and np.array_equal(a.ids, b.ids)
+    # more threads than vertices
+    L1 = oracle_mod.operator_from_dense(np.array([[-1.0, 1.0], [1.0, -1.0]]))
+    F1 = make_field(oracle_mod, [{0: 1.0}, {1: 1.0}], 2)
+    a, _ = oracle_mod.step(L1, F1)
+    b, _ = oracle_mod.step(L1, F1, threads=8)
+    assert np.array_equal(a.vals, b.vals) and np.array_equal(a.rowptr, b.rowptr)
