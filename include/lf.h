@@ -312,9 +312,13 @@ const char* lf_last_error(lf_mesh m);
  * other than LF_F32.
  * The first call on a device looks up the scratch's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  Every call shares the scratch and resets it: calls that overlap on
- * the GPU (other streams, other threads) race and must be serialised by the
- * caller.
+ * capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset it no longer names the array, so do not call this entry
+ * point again in a process that has reset the device.  Every call shares the
+ * scratch and resets it: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  The parameters pass
+ * the checks of lf_create_mesh (finite, dt > 0, mu >= 0, reserved = 0) and
+ * must also be finite in FP32.
  */
 lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers,
                           const int32_t* d_L_rowptr, const int32_t* d_L_colval,

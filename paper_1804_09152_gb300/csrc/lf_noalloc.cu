@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -91,8 +92,14 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers, cons
   lf_params p;
   lf_default_params(&p);
   if (params) p = *params;
+  std::string why;
+  if (!lf::params_valid(p, why)) return noalloc_fail(LF_ERR_INVALID, "lf_step_noalloc: " + why);
   if (p.field_dtype != LF_F32) return noalloc_fail(LF_ERR_INVALID, "lf_step_noalloc stores FP32 values only");
-  if (!(p.dt > 0.0) || !(p.mu >= 0.0)) return noalloc_fail(LF_ERR_INVALID, "dt must be > 0 and mu >= 0");
+  // the kernel computes in FP32: every parameter must stay finite there
+  const double as_float[] = {p.dt, p.mu, p.w_cc, p.w_cb, p.a_cc, p.a_cb, p.e_cc, p.e_cb, p.e_bc};
+  for (double x : as_float)
+    if (!std::isfinite(static_cast<float>(x)))
+      return noalloc_fail(LF_ERR_INVALID, "lf_step_noalloc: a parameter overflows FP32");
 
   void* base = nullptr;
   lf_status s = scratch_address(&base);

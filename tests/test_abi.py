@@ -178,6 +178,12 @@ def test_noalloc_validates_its_arguments_before_any_cuda_call(lib):
     assert call(params=lib.lf_default_params(field_dtype="bf16")) == lib.LF_ERR_INVALID
     assert call(params=lib.lf_default_params(dt=0.0)) == lib.LF_ERR_INVALID
     assert "dt" in lib.lf_last_error(None)
+    for bad in (dict(dt=float("inf")), dict(mu=float("nan")), dict(w_cc=float("nan")), dict(e_bc=-float("inf")),
+                dict(a_cb=1e300), dict(dt=1e39)):
+        assert call(params=lib.lf_default_params(**bad)) == lib.LF_ERR_INVALID, bad
+    bad = lib.lf_default_params()
+    bad.reserved = 1
+    assert call(params=bad) == lib.LF_ERR_INVALID
 
 
 def test_the_product_never_reaches_the_oracle():
