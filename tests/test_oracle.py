@@ -729,3 +729,24 @@ def test_threaded_step_with_matrices_and_tiny_meshes(oracle_mod):
     a, _ = oracle_mod.step(L1, F1)
     b, _ = oracle_mod.step(L1, F1, threads=8)
     assert np.array_equal(a.vals, b.vals) and np.array_equal(a.rowptr, b.rowptr)
+
+
+def test_band_term_is_what_separates_the_fields(oracle_mod):
+    """Sec. 3.1 states that dropping the band term g would remove the
+    separation between the fields.  Under the readings used here (the band
+    term acts between a cell and the base layer, e_cb = -e_bc = e), e = 0
+    leaves every vertex to the base layer after 400 steps, the cells spread
+    thin and never dominate anywhere, while e = .5 (and already e = .1)
+    gives a partition: nearly every vertex belongs to a cell, most with a
+    dominant value above .9."""
+    m = synth.planar_grid(40, jitter=0.2, seed=2)
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    seeds = synth.sample_seeds(m.n_v, 12, 4)
+    res = {}
+    for e in (0.0, 0.1, 0.5):
+        F, _ = oracle_mod.run(L, oracle_mod.seed(m.n_v, seeds), 400, dict(e_cb=e, e_bc=-e))
+        lab, mx = oracle_mod.labels(F, with_max=True)
+        res[e] = (np.mean(lab >= 0), np.mean(mx > 0.9))
+    assert res[0.0] == (0.0, 0.0)
+    for e in (0.1, 0.5):
+        assert res[e][0] > 0.99 and res[e][1] > 0.7, res
