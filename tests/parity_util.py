@@ -137,3 +137,28 @@ def lloyd_differences_explained(got, want, seeds, cand, ties):
                 verts |= {int(got[c]), int(want[c]), int(cand[c]), int(seeds[c])}
                 changed = True
     return sorted(bad - explained)
+
+
+def row_max_err(Fa, Fb):
+    """Per row, the largest absolute difference between two fields over the
+    union of their patterns (an entry missing on one side counts as 0)."""
+    NL = Fa.n_layers
+    ka = coo(Fa.rowptr, Fa.ids, NL)
+    kb = coo(Fb.rowptr, Fb.ids, NL)
+    allk = np.union1d(ka, kb)
+    va = np.zeros(allk.size)
+    vb = np.zeros(allk.size)
+    va[np.searchsorted(allk, ka)] = Fa.vals
+    vb[np.searchsorted(allk, kb)] = Fb.vals
+    out = np.zeros(Fa.n_v)
+    np.maximum.at(out, allk // NL, np.abs(va - vb))
+    return out
+
+
+def one_ring(rowptr, col, mask):
+    """mask grown by one ring of the operator's pattern (rows with an entry
+    in a masked column)."""
+    rows = np.repeat(np.arange(rowptr.size - 1), np.diff(rowptr))
+    out = mask.copy()
+    np.logical_or.at(out, rows, mask[col])
+    return out

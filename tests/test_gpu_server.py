@@ -177,3 +177,33 @@ def test_server_lloyd_rounds_and_dual_mesh_match_the_job_alone(lf):
                     with pytest.raises(lf.LFError) as ei:
                         srv.dual_mesh(jid)
                     assert ei.value.status == lf.LF_ERR_STATE
+
+
+def test_server_job_matches_the_oracle(lf, oracle_mod):
+    """A job through the server against the FP64 oracle directly (not only
+    against the same job alone): icosphere level 3, 16 seeds, 300 steps,
+    served beside two other jobs.  Labels must equal the oracle's on every
+    vertex where a second oracle run, rounded to FP32 after every step, gives
+    the same label (and on its 1-ring): ties aside, bit-exact."""
+    from parity_util import one_ring, to_f32
+    m = synth.icosphere(3)
+    seeds = synth.sample_seeds(m.n_v, 16, 1)
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    F = Fr = oracle_mod.seed(m.n_v, seeds)
+    for _ in range(300):
+        F, _ = oracle_mod.step(L, F)
+        Fr, _ = oracle_mod.step(L, to_f32(Fr, oracle_mod))
+    lab_o = oracle_mod.labels(F)
+    stable = ~one_ring(L.rowptr, L.col, lab_o != oracle_mod.labels(Fr))
+    others = [synth.noisy_torus(40), synth.planar_grid(33, seed=7)]
+    with lf.Server(max_active=3, chunk_steps=64) as srv:
+        ids = [srv.submit(o.V, o.F, synth.sample_seeds(o.n_v, 20, 3 + j), 250) for j, o in enumerate(others)]
+        jid = srv.submit(m.V, m.F, seeds, 300)
+        assert srv.drain(120.0) == lf.LF_OK
+        status, info, labels = srv.wait(jid, 0.0, n_v=m.n_v, release=True)
+        for x in ids:
+            srv.wait(x, 0.0, release=True)
+    assert status == lf.LF_OK
+    assert stable.mean() > 0.8
+    assert np.array_equal(labels[stable], lab_o[stable])
+    assert np.mean(labels == lab_o) > 0.95

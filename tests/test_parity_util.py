@@ -60,3 +60,14 @@ def test_lloyd_differences_need_a_tie():
     # a difference far from the tie stays unexplained
     got4 = np.array([31, 20, 30, 41])
     assert lloyd_differences_explained(got4, want, seeds, cand, [0]) == [1]
+
+
+def test_row_errors_and_rings(oracle_mod):
+    from parity_util import one_ring, row_max_err
+    a = field(oracle_mod, [{0: 1.0}, {0: 0.5, 1: 0.5}, {1: 1.0}], 3)
+    b = field(oracle_mod, [{0: 1.0}, {0: 0.4, 1: 0.5, 2: 0.1}, {2: 1.0}], 3)
+    assert np.allclose(row_max_err(a, b), [0.0, 0.1, 1.0])
+    # path 0 - 1 - 2 - 3: a mark at 3 spreads to 2 only
+    rp = np.array([0, 2, 5, 8, 10])
+    col = np.array([0, 1, 0, 1, 2, 1, 2, 3, 2, 3])
+    assert one_ring(rp, col, np.array([False, False, False, True])).tolist() == [False, False, True, True]
