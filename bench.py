@@ -1,24 +1,29 @@
 #!/usr/bin/env python
 """Layered-field benchmark.
 
-One bench step = one tessellation job on the 512 x 512 jittered planar grid
-(262,144 vertices, 1024 seeds, FP32 field): lf_seed, 2000 time-iterations
-(lf_step) and the sharp labels (lf_labels).  The metric is nnz-updates/s: the
-interest-skeleton entries advanced per second, summed over the job.
+The default line is the batching form: one bench step = 64 tessellation jobs
+(icosphere or noisy torus, 10k-600k vertices each, 10.0 M in all; 32-2048
+seeds; FP32 or BF16 field storage) seeded and advanced 1000 time-iterations
+together by lf_step_batch.  The metric is nnz-updates/s: the
+interest-skeleton entries advanced per second, summed over all jobs; the line
+carries the same jobs stepped one at a time (vs_plain), the roofline of the
+step kernel, the end-to-end figure through the C ABI from host buffers and
+the FP64 oracle timed on the host cores (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME]
 
 Under torchrun every rank runs its own jobs on its own GPU (independent jobs,
 no data-path collective: weak scaling); rank 0 prints one JSON line.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-job on the host cores.
+jobs on every host core.
 
-Other workloads (--workload): torus1024 and torus3300 (noisy tori of 1 M and
-10.9 M vertices), ico3, grid512_shuffled / _reordered / _morton (vertex
-numbering), grid512_general (dense coefficient matrices), batch64 (64 meshes
-in shared launches), serve (a Poisson trace through lf_server),
-grid512_lloyd (Lloyd-like rounds and the dual mesh) and dt_sweep (the time
-step study).
+Other workloads (--workload): grid512 (one 512 x 512 jittered grid, 1024
+seeds, 2000 steps), torus1024 and torus3300 (noisy tori of 1 M and 10.9 M
+vertices), ico3, grid512_shuffled / _reordered / _morton (vertex
+numbering), grid512_general (dense coefficient matrices), serve (the Poisson
+trace through lf_server: p50/p99 job latency), grid512_lloyd (Lloyd-like
+rounds and the dual mesh) and dt_sweep (the time step study).
 """
 import argparse
 import hashlib
@@ -99,8 +104,8 @@ WORKLOADS = {
 # Counters of one step-kernel launch from an ncu capture of the grid512
 # workload (FP32 field, steady state): DRAM bytes and warp instructions.
 # Valid only for that workload and the kernel source they were taken on.
-NCU_COUNTERS = {"workload": "grid512", "dtype": "f32", "kernel_sha": "b677234052a5a212",
-                "bytes_per_launch": 17869056, "warp_instructions_per_launch": 11762763}
+NCU_COUNTERS = {"grid512": {"dtype": "f32", "kernel_sha": "b677234052a5a212",
+                             "bytes_per_launch": 17869056, "warp_instructions_per_launch": 11762763}}
 SM_COUNT, SUBPARTITIONS = 152, 4          # GB300: 152 SMs, 4 schedulers each issuing one warp instruction a cycle
 L2_FLUSH_BYTES = 512 << 20
 
@@ -191,44 +196,110 @@ def aggregate(dist, seconds, units, device):
 ORACLE_SAMPLE_SECONDS = 20.0              # bound on one oracle sample (large meshes take fewer steps)
 
 
-def oracle_sample(wl, n_steps):
-    """The FP64 oracle on the first time steps of the job: n_steps of them,
-    or as many as fit in ORACLE_SAMPLE_SECONDS.  Returns (units, seconds, steps)."""
+def host_cores():
+    """Cores the threaded oracle runs on (it uses every online core)."""
+    return os.cpu_count() or 1
+
+
+class OracleSample:
+    """The FP64 oracle on a bounded sample of a workload's jobs.
+
+    ``jobs`` is a list of (mesh, seeds, coefficient matrices or None).  The
+    operators are built once, before any timing; ``run`` then advances every
+    job from its seeds by ``n_steps`` time steps (or until ``seconds`` have
+    passed) and returns (skeleton entries, seconds, steps taken per job).
+    threads = 0 runs each step on every core (orc_step_threads, the same
+    arithmetic as the single-thread step), 1 the literal single-thread step.
+    """
+
+    def __init__(self, oracle, jobs):
+        self.oracle = oracle
+        self.jobs = []
+        for m, seeds, mats in jobs:
+            L = oracle.cotan_laplacian(m.V, m.F)
+            mats = [M.astype(np.float64) for M in mats] if mats is not None else (None, None, None)
+            self.jobs.append((m.n_v, L, np.asarray(seeds), mats))
+
+    def run(self, n_steps, seconds=ORACLE_SAMPLE_SECONDS, threads=0):
+        units, done = 0, []
+        t = 0.0
+        for n_v, L, seeds, mats in self.jobs:
+            F = self.oracle.seed(n_v, seeds)
+            k = 0
+            while k < n_steps and t < seconds:
+                t0 = time.perf_counter()
+                F, sk = self.oracle.step(L, F, W=mats[0], A=mats[1], E=mats[2], threads=threads)
+                t += time.perf_counter() - t0
+                units += sk
+                k += 1
+            done.append(k)
+            if t >= seconds:
+                break
+        return units, t, done
+
+
+def oracle_sample(jobs):
+    """The one place the benchmark reaches the oracle: its CPU-baseline and
+    reference legs."""
     import oracle
+    return OracleSample(oracle, jobs)
+
+
+def single_mesh_jobs(wl):
     m = wl["mesh"]()
-    L = oracle.cotan_laplacian(m.V, m.F)
-    F = oracle.seed(m.n_v, synth.sample_seeds(m.n_v, wl["k"], wl["seed_stream"]))
-    mats = [M.astype(np.float64) for M in wl["coefs"](wl["k"] + 1)] if wl.get("coefs") else (None, None, None)
-    units, done = 0, 0
-    t0 = time.perf_counter()
-    while done < n_steps and time.perf_counter() - t0 < ORACLE_SAMPLE_SECONDS:
-        F, sk = oracle.step(L, F, W=mats[0], A=mats[1], E=mats[2])
-        units += sk
-        done += 1
-    dt = time.perf_counter() - t0
-    return units, dt, done
+    mats = wl["coefs"](wl["k"] + 1) if wl.get("coefs") else None
+    return [(m, synth.sample_seeds(m.n_v, wl["k"], wl["seed_stream"]), mats)]
 
 
-def run_reference(args, wl):
+def batch_jobs(specs=None):
+    specs = specs or synth.batch_mix()
+    cache, jobs = {}, []
+    for sp in specs:
+        key = (sp.kind, sp.size)
+        if key not in cache:
+            cache[key] = synth.make_mesh(sp)
+        m = cache[key]
+        jobs.append((m, synth.sample_seeds(m.n_v, min(sp.k, m.n_v // 4), sp.seed_stream), None))
+    return jobs
+
+
+def cpu_baseline_line(sampler, n_steps, what, seconds=ORACLE_SAMPLE_SECONDS):
+    """The cpu_baseline object: the threaded oracle on every core, with a
+    short single-thread figure beside it for scale."""
+    units, dt, done = sampler.run(n_steps, seconds, threads=0)
+    u1, dt1, done1 = sampler.run(min(n_steps, 2), min(seconds, 5.0), threads=1)
+    return {"value": units / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": f"{what}: the first {max(done)} time steps of {len(done)} job(s) from their seeds "
+                      f"({sum(done)} job-steps, {dt:.1f} s, literal Algorithm 1 in FP64 over vertex ranges "
+                      f"on {host_cores()} threads)",
+            "single_thread": {"value": u1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"the first {max(done1)} steps of {len(done1)} job(s), {dt1:.1f} s"}}
+
+
+def run_reference(args, jobs, config, n_steps):
+    """The oracle arm: each bench step advances the bounded sample of the
+    workload's jobs on every host core.  Rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sample_steps = args.ref_sample_steps
+    sampler = oracle_sample(jobs)
     vals = []
     for i in range(args.warmup + args.steps):
-        units, dt, done = oracle_sample(wl, sample_steps)
+        units, dt, done = sampler.run(n_steps, ORACLE_SAMPLE_SECONDS, threads=0)
         if i >= args.warmup:
             vals.append((units, dt, done))
     units = sum(v[0] for v in vals)
     secs = sum(v[1] for v in vals)
     value = units / secs
-    sample = f"first {vals[0][2]} of {wl['steps']} time steps of the job per bench step"
+    done = vals[0][2]
+    sample = (f"per bench step: the first {max(done)} time steps of {len(done)} job(s) from their seeds, "
+              f"FP64 oracle on {host_cores()} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(vals),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "desc": wl["desc"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -317,8 +388,9 @@ def run_ours(args, wl):
     t_step = sum(step_ms) / 1e3
     achieved = bytes_total / t_step / 1e9
     peak, peak_kind = measured_peaks()
-    counters = (NCU_COUNTERS if NCU_COUNTERS["kernel_sha"] == kernel_sha() and args.workload == NCU_COUNTERS["workload"]
-                and wl["dtype"] == NCU_COUNTERS["dtype"] else None)
+    counters = NCU_COUNTERS.get(args.workload)
+    if counters and (counters["kernel_sha"] != kernel_sha() or wl["dtype"] != counters["dtype"]):
+        counters = None
     traffic = counters["bytes_per_launch"] if counters else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
@@ -379,10 +451,8 @@ def run_ours(args, wl):
         "wall_s": wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        units_c, dt_c, steps_c = oracle_sample(wl, args.cpu_sample_steps)
-        line["cpu_baseline"] = {"value": units_c / dt_c, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {steps_c} of {T} time steps of one job "
-                                          f"({dt_c:.1f} s, literal Algorithm 1, single thread)"}
+        line["cpu_baseline"] = cpu_baseline_line(oracle_sample(single_mesh_jobs(wl)), args.cpu_sample_steps,
+                                                 f"{args.workload}, {T} time steps per job")
     mesh.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -396,37 +466,42 @@ def _job_bytes(st, n_v):
 
 
 def run_batch(args):
-    """Batching form: 64 mixed jobs (icosphere / noisy torus, 10k-600k vertices,
-    32-2048 seeds, FP32 / BF16) advanced together by lf_step_batch, against the
-    same jobs stepped one at a time with lf_step."""
+    """Batching form, the default line: 64 mixed jobs (icosphere / noisy torus,
+    10k-600k vertices, 32-2048 seeds, FP32 / BF16, 1000 steps) advanced
+    together by lf_step_batch, against the same jobs stepped one at a time
+    with lf_step.  Under torchrun every rank runs the whole mix on its own GPU
+    (independent jobs: weak scaling, no data-path collective)."""
     import torch
     import paper_1804_09152_gb300 as pkg
     pkg.build()
     from paper_1804_09152_gb300 import _lib as lf
 
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
     specs = synth.batch_mix()
     T = specs[0].steps
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    cache = {}
-    meshes, seeds, geo = [], [], []
+    jobs = batch_jobs(specs)
+    geo = [m for m, _, _ in jobs]
+    seeds = [sd for _, sd, _ in jobs]
     with torch.cuda.stream(stream):
         dev = lf.torch_device(stream)
-        for sp in specs:
-            key = (sp.kind, sp.size)
-            if key not in cache:
-                cache[key] = synth.make_mesh(sp)
-            m = cache[key]
-            geo.append(m)
-            meshes.append(lf.Mesh(m.V, m.F, device=dev, field_dtype=sp.dtype))
-            seeds.append(synth.sample_seeds(m.n_v, min(sp.k, m.n_v // 4), sp.seed_stream))
+        meshes = [lf.Mesh(m.V, m.F, device=dev, field_dtype=sp.dtype) for m, sp in zip(geo, specs)]
 
         def seed_all():
             for mesh, sd in zip(meshes, seeds):
                 mesh.seed(sd)
 
         def timed(fn):
-            flush.zero_()
+            flush.zero_()                      # evict L2 before every timed batch
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -439,19 +514,27 @@ def run_batch(args):
         for _ in range(args.warmup):
             seed_all()
             lf.lf_step_batch(meshes, T)
-        times, units, io = [], 0, 0
-        with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        times, units, io, retries = [], 0, 0, 0
+        with ClockSampler(local) as clk:
             for _ in range(args.steps):
                 seed_all()
                 times.append(timed(lambda: lf.lf_step_batch(meshes, T)))
                 sts = [mesh.stats() for mesh in meshes]
                 units += sum(s["skeleton_total"] for s in sts)
                 io += sum(s["nnz_io_total"] * (2 + s["value_bytes"]) for s in sts)
+                retries += sum(s["retries"] for s in sts)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         # the same jobs one at a time
         seed_all()
         t_plain = timed(lambda: [mesh.step(T) for mesh in meshes])
         units_plain = sum(mesh.stats()["skeleton_total"] for mesh in meshes)
-        # end to end from pinned host buffers: create, seed, batch, labels, destroy
+        # end to end through the C ABI from pinned host buffers: create (mesh
+        # upload, device operator build), seed, the batch, labels to the host
         pinned = [(torch.from_numpy(np.ascontiguousarray(m.V)).pin_memory().numpy(),
                    torch.from_numpy(np.ascontiguousarray(m.F)).pin_memory().numpy()) for m in geo]
         torch.cuda.synchronize()
@@ -469,33 +552,62 @@ def run_batch(args):
         t_e2e = time.perf_counter() - t0
         sts = [mesh.stats() for mesh in meshes]
     secs = sum(times)
-    value = units / secs
+    t_all, units_all = aggregate(dist, secs, units, "cuda")
+    value = units_all / t_all
+    # roofline: algorithmic bytes of every job's step (operator, row arrays,
+    # field in and out) over the event-timed steps; one step is one launch
+    # per storage type over all the jobs of that type
+    launches = args.steps * T
     bytes_step = sum(_job_bytes(s, m.n_v) for s, m in zip(sts, geo))
-    achieved = (args.steps * T * bytes_step + io) / secs / 1e9
+    bytes_total = launches * bytes_step + io
+    achieved = bytes_total / secs / 1e9
     peak, peak_kind = measured_peaks()
+    counters = NCU_COUNTERS.get("batch64")
+    if counters and counters["kernel_sha"] != kernel_sha():
+        counters = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": counters["bytes_per_step"] if counters else None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_step": bytes_total / launches, "us_per_step": 1e6 * secs / launches,
+                "launches_per_step": len({sp.dtype for sp in specs})}
+    clk_summary = clk.summary()
+    if counters:
+        mhz = clk_summary.get("sm_mhz") or clk_summary.get("sm_max_mhz") or 2070.0
+        peak_issue = SM_COUNT * SUBPARTITIONS * mhz * 1e6
+        issued = counters["warp_instructions_per_step"] / (secs / launches)
+        roofline["issue"] = {"achieved": issued / 1e12, "peak": peak_issue / 1e12, "unit": "T warp-instr/s",
+                             "frac": issued / peak_issue,
+                             "warp_instructions_per_step": counters["warp_instructions_per_step"]}
     n_v_total = sum(m.n_v for m in geo)
+    config = {"workload": "batch64", "jobs": len(specs), "n_v_total": n_v_total,
+              "time_steps_per_job": T, "bf16_jobs": sum(sp.dtype == "bf16" for sp in specs),
+              "desc": "64 jobs: icosphere level 4-8 or noisy torus (p=1/2), n_v log-uniform 10k-600k, "
+                      "k log-uniform 32-2048, FP32 or BF16 storage with FP32 arithmetic (p=1/2), "
+                      "1000 steps (stream 6); a bench step is the whole batch",
+              "l2": "flushed before every timed batch (512 MiB write); the batch working set exceeds L2"}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+bf16", "data": "synthetic",
-        "config": {"workload": "batch64", "jobs": len(specs), "n_v_total": n_v_total,
-                   "time_steps_per_job": T, "bf16_jobs": sum(sp.dtype == "bf16" for sp in specs),
-                   "desc": "64 jobs: icosphere level 4-8 or noisy torus (p=1/2), n_v log-uniform 10k-600k, "
-                           "k log-uniform 32-2048, FP32 or BF16 (p=1/2), 1000 steps (stream 6)",
-                   "l2": "flushed before every timed batch (512 MiB write); the batch working set exceeds L2"},
-        "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": value / (units_plain / t_plain),
-                     "desc": "the same jobs stepped one after another with lf_step"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind},
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": config,
+        "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99)),
+                       "what": "one batch of 64 jobs, seeds to 1000 steps"},
+        "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": (units / secs) / (units_plain / t_plain),
+                     "desc": "the same jobs stepped one after another with lf_step on this GPU"},
+        "roofline": roofline,
         "e2e": {"value": e2e_units / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(24 * m.n_v + 12 * m.n_f + 4 * len(sd) for m, sd in zip(geo, seeds))),
                 "d2h_bytes_per_step": int(4 * n_v_total), "jobs": len(specs)},
-        "gpu_launches": args.steps * T * 2,
-        "clocks": clk.summary(),
+        "gpu_launches": launches * roofline["launches_per_step"] + retries,
+        "clocks": clk_summary,
     }
     for mesh in meshes:
         mesh.close()
-    print(json.dumps(line), flush=True)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line(oracle_sample(jobs), args.cpu_sample_steps,
+                                                 "batch64, 1000 time steps per job", seconds=15.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def cell_area_stats(m, labels, k):
@@ -655,15 +767,18 @@ def run_dt_sweep(args):
 
 
 def run_serve(args):
-    """Serving form: a prefix of the Poisson trace (200 jobs/s; n_v log-normal
-    in [5k, 2M]; icosphere / torus / grid; 16-8192 seeds; 500-3000 steps)
-    submitted at its arrival times to an lf_server with a 150 GB budget."""
+    """Serving form: the Poisson trace (200 jobs/s by default, 2000 jobs or 60 s;
+    n_v log-normal in [5k, 2M]; icosphere / torus / grid; 16-8192 seeds;
+    500-3000 steps; half the jobs with 5 Lloyd-like rounds and the dual mesh)
+    submitted at its arrival times to an lf_server with a 150 GB budget.
+    --serve-rate sets another arrival rate (the same jobs, arrivals scaled),
+    --serve-jobs a prefix."""
     import torch
     import paper_1804_09152_gb300 as pkg
     pkg.build()
     from paper_1804_09152_gb300 import _lib as lf
 
-    trace = synth.serve_trace()[: args.serve_jobs]
+    trace = synth.serve_trace(rate=args.serve_rate)[: args.serve_jobs]
     cache = {}
     for sp in trace:
         if (sp.kind, sp.size) not in cache:
@@ -691,10 +806,12 @@ def run_serve(args):
                 units += info["skeleton_total"]
             sst = srv.stats()
     wall = (t_end - t0) / 1e9
-    # the same jobs one at a time through lf_step (no arrivals: back to back)
+    # the same jobs one at a time through lf_step (no arrivals: back to back);
+    # the first --plain-jobs of them (the throughput of a prefix)
     t1 = time.perf_counter()
     units_plain = 0
-    for sp, sd in zip(trace, seeds):
+    n_plain = min(len(trace), args.plain_jobs)
+    for sp, sd in zip(trace[:n_plain], seeds[:n_plain]):
         m = cache[(sp.kind, sp.size)]
         with lf.Mesh(m.V, m.F) as mesh:
             mesh.seed(sd)
@@ -711,16 +828,16 @@ def run_serve(args):
         "metric": METRIC, "value": units / wall, "unit": UNIT, "n_gpus": 1, "steps": len(trace), "warmup": 0,
         "ms_per_step": 1e3 * wall / len(trace), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serve", "jobs": len(trace), "arrival_rate_per_s": 200.0,
+        "config": {"workload": "serve", "jobs": len(trace), "arrival_rate_per_s": args.serve_rate,
                    "last_arrival_s": trace[-1].arrival, "hbm_budget_bytes": 150_000_000_000,
                    "lloyd_and_dual_jobs": sum(sp.lloyd_rounds > 0 for sp in trace),
-                   "desc": "first jobs of the Poisson trace (stream 7): n_v log-normal in [5k, 2M], icosphere / "
+                   "desc": "the Poisson trace (stream 7): n_v log-normal in [5k, 2M], icosphere / "
                            "torus / grid, k log-uniform 16-8192, steps U{500..3000}; half the jobs (stream 8) add 5 "
                            "Lloyd-like rounds and the dual mesh; a step of this line is one job"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "jobs_per_s": len(trace) / wall,
         "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": (units / wall) / (units_plain / t_plain),
-                     "desc": "the same jobs back to back, one at a time, lf_create_mesh to lf_labels"},
+                     "desc": f"the first {n_plain} jobs back to back, one at a time, lf_create_mesh to lf_labels"},
         "server": {"peak_running": sst["peak_running"], "peak_bytes": sst["peak_bytes"], "batches": sst["batches"],
                    "busy_s": sst["busy_ns"] / 1e9},
         "e2e": {"value": units / wall, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
@@ -736,22 +853,39 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch64", "serve", "grid512_lloyd", "dt_sweep"],
-                    default="grid512")
+                    default="batch64")
     ap.add_argument("--lloyd-rounds", type=int, default=10)
     ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default=None,
                     help="storage type of the field values (mesh workloads; default: the workload's)")
-    ap.add_argument("--serve-jobs", type=int, default=100)
+    ap.add_argument("--serve-jobs", type=int, default=2000, help="serve: jobs of the trace (it also ends at 60 s)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--plain-jobs", type=int, default=300, help="serve: jobs of the one-at-a-time comparison")
     ap.add_argument("--chunk-steps", type=int, default=0, help="serve: steps between admission rounds (0: default)")
-    ap.add_argument("--cpu-sample-steps", type=int, default=200)
-    ap.add_argument("--ref-sample-steps", type=int, default=40)
+    ap.add_argument("--cpu-sample-steps", type=int, default=None,
+                    help="time steps per job of the CPU-baseline sample (default: 200, 10 for batch64)")
+    ap.add_argument("--ref-sample-steps", type=int, default=None,
+                    help="time steps per job of one reference-arm step (default: 40, 3 for batch64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    batch = args.workload == "batch64"
+    if args.cpu_sample_steps is None:
+        args.cpu_sample_steps = 10 if batch else 200
+    if args.ref_sample_steps is None:
+        args.ref_sample_steps = 3 if batch else 40
+    if args.impl == "reference" and batch:
+        if int(os.environ.get("RANK", "0")) != 0:
+            return None
+        specs = synth.batch_mix()
+        config = {"workload": "batch64", "jobs": len(specs), "time_steps_per_job": specs[0].steps,
+                  "desc": "64 jobs: icosphere level 4-8 or noisy torus (p=1/2), n_v log-uniform 10k-600k, "
+                          "k log-uniform 32-2048, 1000 steps (stream 6); the oracle computes in FP64"}
+        return run_reference(args, batch_jobs(specs), config, args.ref_sample_steps)
     if args.impl == "reference" and args.workload not in WORKLOADS:
         if int(os.environ.get("RANK", "0")) == 0:
-            print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times single-mesh workloads; "
-                              f"{args.workload} is a composite of them"}), flush=True)
+            print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times the batch and the "
+                              f"single-mesh workloads; {args.workload} is a composite of them"}), flush=True)
         return None
-    if args.workload == "batch64":
+    if batch:
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
@@ -764,7 +898,8 @@ def main():
         wl["dtype"] = args.dtype
         wl["desc"] = wl["desc"].replace("FP32 field", f"{args.dtype.upper()} field storage, FP32 arithmetic")
     if args.impl == "reference":
-        run_reference(args, wl)
+        run_reference(args, single_mesh_jobs(wl), {"workload": args.workload, "desc": wl["desc"]},
+                      args.ref_sample_steps)
     else:
         run_ours(args, wl)
 
