@@ -862,14 +862,14 @@ def main():
     ap.add_argument("--plain-jobs", type=int, default=300, help="serve: jobs of the one-at-a-time comparison")
     ap.add_argument("--chunk-steps", type=int, default=0, help="serve: steps between admission rounds (0: default)")
     ap.add_argument("--cpu-sample-steps", type=int, default=None,
-                    help="time steps per job of the CPU-baseline sample (default: 200, 10 for batch64)")
+                    help="time steps per job of the CPU-baseline sample (default: 200, 60 for batch64)")
     ap.add_argument("--ref-sample-steps", type=int, default=None,
                     help="time steps per job of one reference-arm step (default: 40, 3 for batch64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     batch = args.workload == "batch64"
     if args.cpu_sample_steps is None:
-        args.cpu_sample_steps = 10 if batch else 200
+        args.cpu_sample_steps = 60 if batch else 200
     if args.ref_sample_steps is None:
         args.ref_sample_steps = 3 if batch else 40
     if args.impl == "reference" and batch:
