@@ -194,6 +194,7 @@ def aggregate(dist, seconds, units, device):
 
 
 ORACLE_SAMPLE_SECONDS = 20.0              # bound on one oracle sample (large meshes take fewer steps)
+TUNE_AT, TUNE_TRIAL = 100, 32             # batch autotuning: steps before the trials, steps per trial
 
 
 def host_cores():
@@ -511,6 +512,18 @@ def run_batch(args):
             e1.synchronize()
             return e0.elapsed_time(e1) / 1e3
 
+        # the autotuner: per job, after TUNE_AT steps from its seeds (past the
+        # first transient), time both schedules on the job alone and keep the
+        # faster (lf_tune); untimed, reported as tune_s
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter()
+        for mesh, sd in zip(meshes, seeds):
+            mesh.seed(sd)
+            mesh.step(TUNE_AT)
+            mesh.tune(TUNE_TRIAL)
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - t_tune
+        tuned = [mesh.schedule for mesh in meshes]
         for _ in range(args.warmup):
             seed_all()
             lf.lf_step_batch(meshes, T)
@@ -529,7 +542,19 @@ def run_batch(args):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        # the same jobs one at a time
+        # the same batch under one fixed schedule for every job
+        fixed = {}
+        for name in ("lean", "full"):
+            for mesh in meshes:
+                mesh.set_schedule(name)
+            seed_all()
+            lf.lf_step_batch(meshes, T)            # graphs for this grouping
+            seed_all()
+            t_fixed = timed(lambda: lf.lf_step_batch(meshes, T))
+            fixed[name] = sum(mesh.stats()["skeleton_total"] for mesh in meshes) / t_fixed
+        for mesh, sc in zip(meshes, tuned):
+            mesh.set_schedule(sc)
+        # the same jobs one at a time (each under its tuned schedule)
         seed_all()
         t_plain = timed(lambda: [mesh.step(T) for mesh in meshes])
         units_plain = sum(mesh.stats()["skeleton_total"] for mesh in meshes)
@@ -540,7 +565,8 @@ def run_batch(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fresh = [lf.Mesh(V, F, device=dev, field_dtype=sp.dtype) for (V, F), sp in zip(pinned, specs)]
-        for mesh, sd in zip(fresh, seeds):
+        for mesh, sd, sc in zip(fresh, seeds, tuned):
+            mesh.set_schedule(sc)                   # the tuned schedule, as a serving process keeps it
             mesh.seed(sd)
         lf.lf_step_batch(fresh, T)
         e2e_units = 0
@@ -592,6 +618,11 @@ def run_batch(args):
                        "what": "one batch of 64 jobs, seeds to 1000 steps"},
         "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": (units / secs) / (units_plain / t_plain),
                      "desc": "the same jobs stepped one after another with lf_step on this GPU"},
+        "schedules": {"tuned": units / secs, "all_lean": fixed["lean"], "all_full": fixed["full"], "unit": UNIT,
+                      "jobs_lean": tuned.count(0), "jobs_full": tuned.count(1), "tune_s": t_tune,
+                      "desc": f"per job, lf_tune after {TUNE_AT} steps ({TUNE_TRIAL} steps per schedule and round, "
+                              "two rounds) picks the lean or the full step kernel (same bits); the batch under "
+                              "the tuned schedules against every job under one fixed schedule"},
         "roofline": roofline,
         "e2e": {"value": e2e_units / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(24 * m.n_v + 12 * m.n_f + 4 * len(sd) for m, sd in zip(geo, seeds))),

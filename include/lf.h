@@ -328,6 +328,29 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers,
                           int64_t* nnz_out, int64_t* need_tile_cap);
 
 /*
+ * Step-kernel schedules (no counterpart in the paper, which runs one mesh).
+ * Two kernels advance a job with the same bits:
+ *   0 (lean): a three-cell tier for vertices whose closed neighbourhood
+ *     holds at most three cells, each row at most one cell and then the base
+ *     layer (the steady state), and the storage-free tier for the rest --
+ *     fast where that shape holds everywhere, slow wherever it does not;
+ *   1 (full, the default): register-map, shared-memory and storage-free
+ *     tiers.
+ * Jobs with coefficient matrices always take the general form of the full
+ * kernel.  lf_set_schedule fixes a job's schedule; lf_schedule reads it (-1
+ * for NULL).  lf_tune is the autotuner: it runs trial_steps time-iterations
+ * under each schedule twice (in alternating order), timed with CUDA events on
+ * the mesh's stream, keeps the fastest for the job and returns it in
+ * *schedule (nullable).  The trial steps advance the job like lf_step (they
+ * count in its steps and statistics).  lf_step and lf_step_batch run each job
+ * under its schedule; a batch launches once per step for every storage type
+ * and schedule present.
+ */
+lf_status lf_set_schedule(lf_mesh m, int32_t schedule);
+int32_t lf_schedule(lf_mesh m);
+lf_status lf_tune(lf_mesh m, int32_t trial_steps, int32_t* schedule);
+
+/*
  * Lloyd-like iterations (Sec. 5): `rounds` times, new seeds from the current
  * field, a fresh field from them (as lf_seed) and steps_per_round steps (as
  * lf_step).  A cell is the set of vertices with an entry of its layer; its

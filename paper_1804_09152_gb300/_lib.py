@@ -122,6 +122,12 @@ _lib.lf_last_error.argtypes = [_P]
 _lib.lf_last_error.restype = ctypes.c_char_p
 _lib.lf_step_batch.argtypes = [ctypes.POINTER(_P), _i32, ctypes.POINTER(_i32)]
 _lib.lf_step_batch.restype = ctypes.c_int
+_lib.lf_set_schedule.argtypes = [_P, _i32]
+_lib.lf_set_schedule.restype = ctypes.c_int
+_lib.lf_schedule.argtypes = [_P]
+_lib.lf_schedule.restype = _i32
+_lib.lf_tune.argtypes = [_P, _i32, ctypes.POINTER(_i32)]
+_lib.lf_tune.restype = ctypes.c_int
 _lib.lf_step_noalloc.argtypes = [_P, _i32, _i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _i32,
                                  ctypes.POINTER(lf_params), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
 _lib.lf_step_noalloc.restype = ctypes.c_int
@@ -150,7 +156,7 @@ _lib.lf_server_destroy.restype = None
 EXPORTED = ["lf_default_params", "lf_create_mesh", "lf_create_mesh_csr", "lf_seed", "lf_seed_regions",
             "lf_set_coefficients", "lf_step", "lf_labels",
             "lf_get_operator", "lf_get_field", "lf_set_field", "lf_stats", "lf_destroy_mesh", "lf_status_string", "lf_last_error",
-            "lf_step_noalloc", "lf_step_batch", "lf_lloyd", "lf_extract_dual", "lf_server_default_params", "lf_server_create",
+            "lf_step_noalloc", "lf_step_batch", "lf_set_schedule", "lf_schedule", "lf_tune", "lf_lloyd", "lf_extract_dual", "lf_server_default_params", "lf_server_create",
             "lf_server_submit", "lf_server_wait", "lf_server_dual_mesh", "lf_server_drain", "lf_server_stats", "lf_server_destroy"]
 
 
@@ -254,6 +260,23 @@ def lf_set_coefficients(mesh, n_layers, W=None, A=None, E=None):
 
 def lf_step(mesh, n_iters):
     _check(_lib.lf_step(mesh, int(n_iters)), mesh)
+
+
+SCHEDULES = {"lean": 0, "full": 1}
+
+
+def lf_set_schedule(mesh, schedule):
+    _check(_lib.lf_set_schedule(mesh, SCHEDULES.get(schedule, schedule)), mesh)
+
+
+def lf_schedule(mesh):
+    return int(_lib.lf_schedule(mesh))
+
+
+def lf_tune(mesh, trial_steps):
+    out = _i32(-1)
+    _check(_lib.lf_tune(mesh, int(trial_steps), ctypes.byref(out)), mesh)
+    return int(out.value)
 
 
 def lf_step_batch(meshes, n_iters):
@@ -386,6 +409,18 @@ class Mesh:
 
     def step(self, n):
         lf_step(self.h, n)
+
+    def set_schedule(self, schedule):
+        """0 / "lean" or 1 / "full" (the same bits either way)."""
+        lf_set_schedule(self.h, schedule)
+
+    @property
+    def schedule(self):
+        return lf_schedule(self.h)
+
+    def tune(self, trial_steps=128):
+        """The autotuner: times each schedule on this job (advancing it) and keeps the fastest."""
+        return lf_tune(self.h, trial_steps)
 
     def labels(self, with_max=False):
         return lf_labels(self.h, self.n_v, with_max)

@@ -46,6 +46,7 @@ struct lf_mesh_s {
   int64_t n_v = 0;
   int64_t L_nnz = 0;
   int dtype = 0;
+  int sched = lf::kSchedFull;    // step-kernel schedule (lf_set_schedule, lf_tune)
   int n_layers = 0;
   int num_tiles = 0;
   int64_t tile_cap = 0;          // entries per tile segment
@@ -68,6 +69,7 @@ struct lf_mesh_s {
 
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // step graphs by starting parity
   lf::BatchParams gparams[2]{};                     // the launch parameters each was built with
+  int gkind[2] = {-1, -1};                          // and the launch kind
 
   // general coefficient matrices (lf_set_coefficients): one device block of
   // up to three n_layers x n_layers FP32 matrices for that layer count
@@ -363,7 +365,8 @@ const char* failed_step_message(uint32_t err) {
 }
 
 // A graph of independent chains, each of kGraphSteps step launches of one
-// storage type (chain c launches chains[c].second with step = 0, 1, ...).
+// launch kind -- storage type and schedule -- (chain c launches
+// chains[c].second with step = 0, 1, ...).
 // Within a chain each launch is joined to the previous one by a programmatic
 // edge: it may start its CTAs while the previous one drains, and waits inside
 // the kernel (griddepcontrol.wait) before it reads the previous step's output.
@@ -375,14 +378,14 @@ cudaError_t make_step_graph(const std::vector<std::pair<int, lf::BatchParams>>& 
   std::vector<lf::BatchParams> params;
   params.reserve(chains.size() * kGraphSteps);
   for (size_t c = 0; c < chains.size() && e == cudaSuccess; ++c) {
-    const int dtype = chains[c].first;
+    const int kind = chains[c].first;
     cudaGraphNode_t prev = nullptr;
     for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) {
       params.push_back(chains[c].second);
       params.back().step = s;
       void* args[1] = {&params.back()};
       cudaKernelNodeParams kp{};
-      kp.func = const_cast<void*>(lf::step_kernel(dtype, lf::needs_general(chains[c].second)));
+      kp.func = const_cast<void*>(lf::step_kernel(kind, lf::needs_general(chains[c].second)));
       kp.gridDim = dim3(static_cast<unsigned>(chains[c].second.tile_start[chains[c].second.n_jobs]));
       kp.blockDim = dim3(static_cast<unsigned>(lf::kTile));
       kp.sharedMemBytes = 0;
@@ -411,16 +414,18 @@ cudaError_t make_step_graph(const std::vector<std::pair<int, lf::BatchParams>>& 
 lf_status build_graph(lf_mesh m) {
   const int par = static_cast<int>(m->h_st.epoch & 1u);
   const lf::BatchParams p = single_job_params(m, kGraphSteps);
+  const int kind = lf::step_kind(m->dtype, m->sched);
   if (m->gexec[par]) {
-    if (std::memcmp(&p, &m->gparams[par], sizeof(p)) == 0) return LF_OK;
+    if (std::memcmp(&p, &m->gparams[par], sizeof(p)) == 0 && m->gkind[par] == kind) return LF_OK;
     cudaGraphExecDestroy(m->gexec[par]);
     m->gexec[par] = nullptr;
   }
   std::vector<std::pair<int, lf::BatchParams>> chains;
-  chains.emplace_back(m->dtype, p);
+  chains.emplace_back(kind, p);
   cudaError_t e = make_step_graph(chains, &m->gexec[par]);
   if (e != cudaSuccess) return cuda_fail(m, e, "building the step graph");
   m->gparams[par] = p;
+  m->gkind[par] = kind;
   return LF_OK;
 }
 
@@ -889,7 +894,7 @@ lf_status lf_step(lf_mesh m, int32_t n_iters) {
       lf::BatchParams p = single_job_params(m, static_cast<int>(todo - launched));
       for (int s2 = 0; launched < todo; ++launched, ++s2) {
         p.step = s2;
-        LF_CUDA(m, lf::launch_step(p, m->dtype, m->stream));
+        LF_CUDA(m, lf::launch_step(p, lf::step_kind(m->dtype, m->sched), m->stream));
       }
     }
     s = read_status(m);
@@ -941,7 +946,7 @@ lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters) {
     if (s != LF_OK) return s;
     target[static_cast<size_t>(a)] = meshes[a]->steps + n_iters[a];
   }
-  // one chain of launches per storage type present; the graph is rebuilt
+  // one chain of launches per storage type and schedule present; the graph is rebuilt
   // whenever the parameters of a chain change (members, buffers, parity)
   cudaGraphExec_t gexec = nullptr;
   std::vector<std::pair<int, lf::BatchParams>> gkey;
@@ -961,13 +966,13 @@ lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters) {
     }
     if (active == 0) break;
     std::vector<std::pair<int, lf::BatchParams>> chains;
-    for (int dtype = 0; dtype < 3; ++dtype) {
+    for (int kind = 0; kind < 3 * lf::kSchedules; ++kind) {
       lf::BatchParams p;
       std::memset(&p, 0, sizeof(p));
       int tiles = 0;
       for (int32_t a = 0; a < n; ++a) {
         lf_mesh m = meshes[a];
-        if (m->dtype != dtype || target[static_cast<size_t>(a)] == m->steps) continue;
+        if (lf::step_kind(m->dtype, m->sched) != kind || target[static_cast<size_t>(a)] == m->steps) continue;
         const int j = p.n_jobs++;
         p.tile_start[j] = tiles;
         tiles += m->num_tiles;
@@ -976,7 +981,7 @@ lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters) {
         p.job[j].steps = static_cast<int32_t>(todo);
       }
       p.tile_start[p.n_jobs] = tiles;
-      if (p.n_jobs > 0) chains.emplace_back(dtype, p);
+      if (p.n_jobs > 0) chains.emplace_back(kind, p);
     }
     int64_t launched = 0;
     if (todo >= kGraphSteps) {
@@ -1035,6 +1040,61 @@ lf_status lf_step_batch(lf_mesh* meshes, int32_t n, const int32_t* n_iters) {
   }
   drop_graph();
   return result;
+}
+
+lf_status lf_set_schedule(lf_mesh m, int32_t schedule) {
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (schedule < 0 || schedule >= lf::kSchedules) return fail(m, LF_ERR_INVALID, "unknown schedule");
+  m->sched = schedule;
+  return LF_OK;
+}
+
+int32_t lf_schedule(lf_mesh m) { return m ? m->sched : -1; }
+
+lf_status lf_tune(lf_mesh m, int32_t trial_steps, int32_t* schedule) {
+  lf::TraceRange trace("lf_tune");
+  lf_status s = check_usable(m);
+  if (s != LF_OK) return s;
+  if (trial_steps < 1) return fail(m, LF_ERR_INVALID, "trial_steps must be >= 1");
+  if (m->n_layers == 0) return fail(m, LF_ERR_STATE, "lf_seed or lf_set_field must come first");
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  for (auto& e : ev) {
+    cudaError_t ce = cudaEventCreate(&e);
+    if (ce != cudaSuccess) {
+      for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+      return cuda_fail(m, ce, "cudaEventCreate");
+    }
+  }
+  // two rounds over the schedules, the second in reverse order, so that a
+  // trend along the trajectory weighs on every schedule alike; every trial
+  // advances the job (the schedules give the same bits)
+  float ms[lf::kSchedules] = {};
+  for (int r = 0; r < 2 && s == LF_OK; ++r) {
+    for (int k = 0; k < lf::kSchedules && s == LF_OK; ++k) {
+      const int sc = (r == 0) ? k : lf::kSchedules - 1 - k;
+      m->sched = sc;
+      s = build_graph(m);                  // outside the timing
+      if (s != LF_OK) break;
+      cudaError_t ce = cudaEventRecord(ev[0], m->stream);
+      if (ce == cudaSuccess) s = lf_step(m, trial_steps);
+      if (ce == cudaSuccess && s == LF_OK) ce = cudaEventRecord(ev[1], m->stream);
+      if (ce == cudaSuccess && s == LF_OK) ce = cudaEventSynchronize(ev[1]);
+      float t = 0.0f;
+      if (ce == cudaSuccess && s == LF_OK) ce = cudaEventElapsedTime(&t, ev[0], ev[1]);
+      if (ce != cudaSuccess && s == LF_OK) s = cuda_fail(m, ce, "timing a schedule");
+      ms[sc] += t;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (s != LF_OK) return s;
+  int best = 0;
+  for (int k = 1; k < lf::kSchedules; ++k)
+    if (ms[k] < ms[best]) best = k;
+  m->sched = best;
+  if (schedule) *schedule = best;
+  return LF_OK;
 }
 
 lf_status lf_labels(lf_mesh m, int32_t* labels, float* maxval) {

@@ -110,11 +110,18 @@ int step_slots();
 // Kernel entry of the step for a storage type (0 f32, 1 bf16, 2 f16), in
 // the form for general coefficient matrices or not; its only argument is a
 // BatchParams.
-const void* step_kernel(int dtype, bool general);
+// Step-kernel schedules.  Both give the same bits; which is faster depends on
+// the job (how much of its neighbourhood the three-cell tier covers).
+constexpr int kSchedLean = 0;   // three-cell tier, storage-free tier for the rest
+constexpr int kSchedFull = 1;   // three-cell tier is not used: register map, shared-memory map, storage-free
+constexpr int kSchedules = 2;
+// A launch kind: the storage type and the schedule of the jobs in one launch.
+inline int step_kind(int dtype, int sched) { return dtype + 3 * sched; }
+const void* step_kernel(int kind, bool general);
 // True when a job of the launch has general coefficient matrices.
 bool needs_general(const BatchParams& p);
 // One step launch over the jobs in p, with programmatic stream serialisation.
-cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s);
+cudaError_t launch_step(const BatchParams& p, int kind, cudaStream_t s);
 // The seed and label kernels take one job by value.
 cudaError_t launch_seed(const JobDesc& job, int k, const int32_t* d_seeds, int dtype, cudaStream_t s);
 cudaError_t launch_labels(const JobDesc& job, int buf, int dtype, int32_t* d_labels, float* d_maxval,

@@ -89,7 +89,8 @@ constexpr int kBlock = kTile;   // threads (= vertices) per CTA
 #define LF_SLOTS 5
 #endif
 constexpr int kSlots = LF_SLOTS; // register map slots of the fast path
-constexpr int kChunk = 2;       // neighbours fetched per batch
+constexpr int kChunk = 2;       // neighbours fetched per batch on the register-map tier
+constexpr int kChunk0 = 4;      // neighbours fetched per batch on the three-cell tier
 constexpr int kPool = 4;        // medium-path maps per CTA
 constexpr int kMed = 32;        // slots of a medium-path map
 
@@ -410,6 +411,108 @@ struct MedMap {
   }
 };
 
+
+// Runs fn with the number of register slots a warp's lanes use at most, for
+// the three-cell tier (three cells and the base layer at most).
+template <class Fn>
+__device__ __forceinline__ void with_slots4(int n, Fn&& fn) {
+  switch (n) {
+    case 1: fn(std::integral_constant<int, 1>{}); break;
+    case 2: fn(std::integral_constant<int, 2>{}); break;
+    case 3: fn(std::integral_constant<int, 3>{}); break;
+    default: fn(std::integral_constant<int, 4>{}); break;
+  }
+}
+
+// The update over a register map of N live slots, shared by the register-map
+// and three-cell tiers: the diagonal term of the own entries, ascending slot
+// order, the skeleton test, the per-vertex sums, Algorithm 1's update (the
+// class closed form or the general matrices), the clamp, the normalisation
+// and the rounding to the storage type.
+template <int DT, bool GEN, int N>
+__device__ __forceinline__ void slot_update(SlotMap& mp, const int own_cells, const int own, const float dsum,
+                                            const int base, const Coefs& c, const GenCoef& gc, const bool general,
+                                            VertexSums& S, float (&vnew)[kSlots], bool (&keep)[kSlots], int& kept,
+                                            float& tot, bool& zero_sum) {
+  using V = Val<DT>;
+    // diagonal: the own entries (the own cells, then the base layer)
+#pragma unroll
+    for (int s = 0; s < N; ++s)
+      if (s < own_cells || (s == mp.cnt - 1 && own_cells < own)) mp.g[s] = fmaf(-dsum, mp.f[s], mp.g[s]);
+    // slots in ascending layer order (empty slots, id -1, last): the sums
+    // below then run in the same order as on the other paths, and the row
+    // is written in slot order
+    mp.template sort_first<(N < kSlots - 1 ? N : kSlots - 1)>();
+    float sq[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) sq[s] = root(mp.f[s]);
+    bool ins[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      ins[s] = s < mp.cnt && in_skeleton(mp.f[s], mp.g[s]);
+      if (ins[s]) add_to_sums(S, mp.id[s] == base, mp.f[s], mp.g[s], sq[s]);
+    }
+    if (general) {
+      const float fn = static_cast<float>(S.nC + S.hasb);
+      float Aj[N], Wj[N], Ej[N];
+      float sumA = 0.0f, sumW = 0.0f;
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        Aj[s] = Wj[s] = Ej[s] = 0.0f;
+        if (ins[s]) {
+#pragma unroll
+          for (int l = 0; l < N; ++l) {
+            if (ins[l]) {
+              Aj[s] = __fmaf_rn(gc.a(mp.id[s], mp.id[l]), mp.g[l], Aj[s]);
+              Wj[s] = __fmaf_rn(gc.w(mp.id[s], mp.id[l]), mp.f[l], Wj[s]);
+              Ej[s] = __fmaf_rn(gc.e(mp.id[s], mp.id[l]), sq[l], Ej[s]);
+            }
+          }
+          sumA = __fadd_rn(sumA, Aj[s]);
+          sumW = __fadd_rn(sumW, Wj[s]);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        if (ins[s]) {
+          vnew[s] = gc.value(mp.f[s], sq[s], Aj[s], Wj[s], Ej[s], sumA, sumW, fn);
+          tot += vnew[s];
+        }
+      }
+    } else {
+      const Update U(S, c);
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        if (ins[s]) {
+          vnew[s] = U.value(mp.id[s] == base, mp.f[s], mp.g[s], sq[s], S, c);
+          tot += vnew[s];
+        }
+      }
+    }
+    if (!(tot > 0.0f)) zero_sum = true;
+    const float rtot = 1.0f / tot;           // normalisation: one division per vertex
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      if (ins[s]) {
+        const float vs = V::widen(V::round(__fmul_rn(vnew[s], rtot)));
+        if (vs != 0.0f) { keep[s] = true; vnew[s] = vs; ++kept; }
+      }
+    }
+}
+
+// Writes the kept entries of a register map of N slots in slot order.
+template <int DT, int N, class Put>
+__device__ __forceinline__ void slot_write(const SlotMap& mp, const bool (&keep)[kSlots], const float (&vnew)[kSlots],
+                                           int off, Put& put) {
+  using V = Val<DT>;
+  int o = off;
+#pragma unroll
+  for (int s = 0; s < N; ++s) {
+    if (!keep[s]) continue;
+    put(o, mp.id[s], V::round(vnew[s]));
+    ++o;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // the step kernel
@@ -751,70 +854,8 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
       // count is within it, whichever lanes run this together)
       // (the general form keeps all slots: its matrix sums are the cost there)
       with_slots(GEN ? kSlots : __reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
-      constexpr int N = decltype(slots)::value;
-      // diagonal: the own entries (the own cells, then the base layer)
-#pragma unroll
-      for (int s = 0; s < N; ++s)
-        if (s < own_cells || (s == mp.cnt - 1 && own_cells < own)) mp.g[s] = fmaf(-nb.dsum, mp.f[s], mp.g[s]);
-      // slots in ascending layer order (empty slots, id -1, last): the sums
-      // below then run in the same order as on the other paths, and the row
-      // is written in slot order
-      mp.template sort_first<(N < kSlots - 1 ? N : kSlots - 1)>();
-      float sq[N];
-#pragma unroll
-      for (int s = 0; s < N; ++s) sq[s] = root(mp.f[s]);
-      bool ins[N];
-#pragma unroll
-      for (int s = 0; s < N; ++s) {
-        ins[s] = s < mp.cnt && in_skeleton(mp.f[s], mp.g[s]);
-        if (ins[s]) add_to_sums(S, mp.id[s] == base, mp.f[s], mp.g[s], sq[s]);
-      }
-      if (general) {
-        const float fn = static_cast<float>(S.nC + S.hasb);
-        float Aj[N], Wj[N], Ej[N];
-        float sumA = 0.0f, sumW = 0.0f;
-#pragma unroll
-        for (int s = 0; s < N; ++s) {
-          Aj[s] = Wj[s] = Ej[s] = 0.0f;
-          if (ins[s]) {
-#pragma unroll
-            for (int l = 0; l < N; ++l) {
-              if (ins[l]) {
-                Aj[s] = __fmaf_rn(gc.a(mp.id[s], mp.id[l]), mp.g[l], Aj[s]);
-                Wj[s] = __fmaf_rn(gc.w(mp.id[s], mp.id[l]), mp.f[l], Wj[s]);
-                Ej[s] = __fmaf_rn(gc.e(mp.id[s], mp.id[l]), sq[l], Ej[s]);
-              }
-            }
-            sumA = __fadd_rn(sumA, Aj[s]);
-            sumW = __fadd_rn(sumW, Wj[s]);
-          }
-        }
-#pragma unroll
-        for (int s = 0; s < N; ++s) {
-          if (ins[s]) {
-            vnew[s] = gc.value(mp.f[s], sq[s], Aj[s], Wj[s], Ej[s], sumA, sumW, fn);
-            tot += vnew[s];
-          }
-        }
-      } else {
-        const Update U(S, c);
-#pragma unroll
-        for (int s = 0; s < N; ++s) {
-          if (ins[s]) {
-            vnew[s] = U.value(mp.id[s] == base, mp.f[s], mp.g[s], sq[s], S, c);
-            tot += vnew[s];
-          }
-        }
-      }
-      if (!(tot > 0.0f)) zero_sum = true;
-      const float rtot = 1.0f / tot;           // normalisation: one division per vertex
-#pragma unroll
-      for (int s = 0; s < N; ++s) {
-        if (ins[s]) {
-          const float vs = V::widen(V::round(__fmul_rn(vnew[s], rtot)));
-          if (vs != 0.0f) { keep[s] = true; vnew[s] = vs; ++kept; }
-        }
-      }
+        slot_update<DT, GEN, decltype(slots)::value>(mp, own_cells, own, nb.dsum, base, c, gc, general, S, vnew, keep,
+                                                     kept, tot, zero_sum);
       });
     } else if (mode == kMedium) {
       // ---- medium path: the same update over the shared-memory map ----------
@@ -962,13 +1003,7 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) top = keep[s] ? s + 1 : top;
       with_slots(GEN ? kSlots : __reduce_max_sync(__activemask(), top), [&](auto slots) {
-        int o = off;
-#pragma unroll
-        for (int s = 0; s < decltype(slots)::value; ++s) {
-          if (!keep[s]) continue;
-          put(o, mp.id[s], V::round(vnew[s]));
-          ++o;
-        }
+        slot_write<DT, decltype(slots)::value>(mp, keep, vnew, off, put);
       });
     } else if (mode == kMedium) {
       int o = off;
@@ -987,6 +1022,310 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
         if (!in_skeleton(F, G)) continue;
         const float v = general ? slow_general_value(nb, gc, l, F, gsumA, gsumW, fn) : U.value(l == base, F, G, root(F), S, c);
         const T vt = V::round(__fmul_rn(v, 1.0f / tot));
+        if (V::widen(vt) != 0.0f) {
+          put(o, l, vt);
+          ++o;
+        }
+      }
+    }
+    out.head[i] = ho;
+  }
+
+  // ---- end of step: the last CTA of the job commits the step ----------------
+  if (t == 0) {
+    atomicAdd(&st->skeleton_step, static_cast<unsigned long long>(tile_sk));
+    atomicAdd(&st->nnz_step, static_cast<unsigned long long>(tile_total));
+    __threadfence();
+    const uint32_t prev = atomicAdd(&st->done, 1u);
+    if (prev == static_cast<uint32_t>(J.num_tiles) - 1u) {
+      __threadfence();
+      if (ld_relaxed_u32(&st->err) == 0u) {
+        const unsigned long long nin = ld_relaxed(&st->nnz);
+        const unsigned long long nout = ld_relaxed(&st->nnz_step);
+        st->skeleton_total = ld_relaxed(&st->skeleton_total) + ld_relaxed(&st->skeleton_step);
+        st->nnz_io_total = ld_relaxed(&st->nnz_io_total) + nin + nout;
+        st->nnz = nout;
+        st->epoch = st->epoch + 1u;
+      }
+      st->skeleton_step = 0ull;
+      st->nnz_step = 0ull;
+      st->done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the lean step kernel (class coefficients): the three-cell tier, and the
+// storage-free tier for every vertex outside it
+// ---------------------------------------------------------------------------
+// The same time-iteration as step_kernel_impl, for the steady-state shape
+// that nearly every vertex takes once the cells have formed: every row of the
+// closed neighbourhood holds at most one cell and then the base layer, and
+// the neighbourhood holds at most three cells.  Three cell sums and the base
+// sum are kept in registers; a neighbour's cell either matches a slot or
+// opens the next one, each sum taken in the order of the row of L exactly as
+// on the register-map tier.  A vertex outside the shape takes the
+// storage-free tier (the union in increasing id order by repeated minimum
+// search).  Every tier rounds every operation explicitly in the same order,
+// so the result is bit for bit that of step_kernel_impl; without the
+// register-map and shared-memory tiers the kernel is smaller, and it is the
+// faster of the two where the shape holds nearly everywhere.
+template <int DT>
+__global__ void __launch_bounds__(kBlock, 4) step_kernel_lean(const __grid_constant__ BatchParams P) {
+  using V = Val<DT>;
+  using T = typename V::T;
+  constexpr int kWarps = kBlock / 32;
+  __shared__ uint32_t s_err;
+  __shared__ unsigned s_red[kWarps];
+  __shared__ int s_warp_cnt[kWarps];
+
+  wait_previous_grid();
+  allow_next_grid();
+
+  int lo = 0, hi = P.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.tile_start[mid] <= static_cast<int>(blockIdx.x)) lo = mid; else hi = mid - 1;
+  }
+  const JobDesc& J = P.job[lo];
+  if (P.step >= J.steps) return;
+
+  const int t = threadIdx.x;
+  const int lane = t & 31;
+  const int warp = t >> 5;
+  const int tile = static_cast<int>(blockIdx.x) - P.tile_start[lo];
+  const int n_v = J.n_v;
+  const int base = J.n_layers - 1;
+  const int cap = J.tile_cap;
+  const int par = (J.parity0 + P.step) & 1;
+  const FieldBuf in = J.buf[par];
+  const FieldBuf out = J.buf[par ^ 1];
+  const Coefs& c = J.c;
+  DevStatus* st = J.st;
+
+  Neighbourhood<DT> nb;
+  nb.rows = in.rows;
+  nb.Fid = in.ids;
+  nb.Fval = static_cast<const T*>(in.vals);
+  nb.Lcv = J.L_colval;
+  nb.dsum = 0.0f;
+  nb.p0 = nb.p1 = nb.q0 = nb.q1 = 0;
+#ifdef LF_CHECKED
+  nb.st = J.st;
+  nb.n_v = J.n_v;
+  nb.L_nnz = J.L_nnz;
+  nb.entries = J.num_tiles * J.tile_cap;
+#endif
+
+  const int i = tile * kBlock + t;
+  int4 h_own = make_int4(0, 0, 0, 0);
+  if (i < n_v) {
+    h_own = __ldg(in.head + i);
+    nb.q0 = __ldg(J.L_rowptr + i);
+    nb.q1 = __ldg(J.L_rowptr + i + 1);
+  }
+  if (t == 0) s_err = ld_relaxed_u32(&st->err);
+  __syncthreads();
+  if (s_err) return;                 // an earlier step of this job failed
+
+  SlotMap mp;
+  mp.clear();
+  bool zero_sum = false;
+  int kept = 0, nsk = 0;
+  const int own = h_own.x;
+  float vnew[kSlots];
+  bool keep[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) { vnew[s] = 0.0f; keep[s] = false; }
+  VertexSums S = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, 0};
+  float tot = 0.0f;
+  int own_cells = own;
+  bool done0 = false;
+  bool summed = false;               // nb.dsum holds the row sum of L
+  {
+    const int e0o = h_own.y & 0xffff;
+    const int e1o = (h_own.y >> 16) & 0xffff;
+    const bool own_simple = i < n_v && own <= 2 && (own < 2 || e1o == base);
+    if (__any_sync(0xffffffffu, own_simple) && own_simple) {
+      int c0 = -1, c1 = -1, c2 = -1;
+      float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, gb = 0.0f, ds = 0.0f, f0 = 0.0f, fb = 0.0f;
+      int ownc = 0;
+      if (own >= 1) {
+        if (e0o == base) {
+          fb = V::from_bits(h_own.z);
+        } else {
+          c0 = e0o;
+          f0 = V::from_bits(h_own.z);
+          ownc = 1;
+        }
+      }
+      if (own == 2) fb = V::from_bits(h_own.w);
+      bool ok = true;
+      for (int qb = nb.q0; qb < nb.q1; qb += kChunk0) {
+        int2 cv[kChunk0];
+#pragma unroll
+        for (int k = 0; k < kChunk0; ++k) {
+          cv[k] = make_int2(-1, 0);
+          if (qb + k < nb.q1) cv[k] = __ldg(nb.Lcv + LF_CK(nb, qb + k, nb.L_nnz));
+        }
+        int4 hj[kChunk0];
+#pragma unroll
+        for (int k = 0; k < kChunk0; ++k) {
+          hj[k] = make_int4(0, 0, 0, 0);
+          if (cv[k].x >= 0) hj[k] = __ldg(in.head + LF_CK(nb, cv[k].x, nb.n_v));
+        }
+#pragma unroll
+        for (int k = 0; k < kChunk0; ++k) {
+          if (cv[k].x < 0) continue;
+          const float lij = __int_as_float(cv[k].y);
+          ds += lij;
+          const int rn = hj[k].x;
+          const int e0 = hj[k].y & 0xffff;
+          const int e1 = (hj[k].y >> 16) & 0xffff;
+          ok = ok && rn <= 2 && (rn < 2 || e1 == base);
+          const float x0 = __fmul_rn(lij, V::from_bits(hj[k].z));
+          const float x1 = __fmul_rn(lij, V::from_bits(hj[k].w));
+          // the base entry: the only entry, or the second one
+          const bool b0 = rn >= 1 && e0 == base;
+          gb = b0 ? __fadd_rn(gb, x0) : gb;
+          gb = (rn == 2 && e1 == base) ? __fadd_rn(gb, x1) : gb;
+          // the cell entry: the first one, unless it is the base
+          const int cell = (rn >= 1 && !b0) ? e0 : -2;
+          const bool m0 = cell == c0, m1 = cell == c1, m2 = cell == c2;
+          const bool fresh = cell >= 0 && !m0 && !m1 && !m2;
+          const bool o0 = fresh && c0 < 0;
+          const bool o1 = fresh && c0 >= 0 && c1 < 0;
+          const bool o2 = fresh && c1 >= 0 && c2 < 0;
+          ok = ok && !(fresh && c2 >= 0);
+          g0 = o0 ? x0 : (m0 ? __fadd_rn(g0, x0) : g0);
+          g1 = o1 ? x0 : (m1 ? __fadd_rn(g1, x0) : g1);
+          g2 = o2 ? x0 : (m2 ? __fadd_rn(g2, x0) : g2);
+          c0 = o0 ? cell : c0;
+          c1 = o1 ? cell : c1;
+          c2 = o2 ? cell : c2;
+        }
+      }
+      nb.dsum = ds;                  // the whole row was read either way
+      summed = true;
+      if (ok) {
+        done0 = true;
+        own_cells = ownc;
+        mp.id[0] = c0; mp.g[0] = g0; mp.f[0] = f0;
+        mp.id[1] = c1; mp.g[1] = g1;
+        mp.id[2] = c2; mp.g[2] = g2;
+        const int ncell = (c0 >= 0) + (c1 >= 0) + (c2 >= 0);
+        // the base layer joins the slots last (largest id)
+#pragma unroll
+        for (int s2 = 0; s2 < kSlots; ++s2) {
+          if (s2 == ncell) { mp.id[s2] = base; mp.g[s2] = gb; mp.f[s2] = fb; }
+        }
+        mp.cnt = ncell + 1;
+      }
+    }
+  }
+
+  const GenCoef gc{};                // unused: class coefficients only
+  if (i < n_v) {
+    if (done0) {
+      with_slots4(__reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
+        slot_update<DT, false, decltype(slots)::value>(mp, own_cells, own, nb.dsum, base, c, gc, false, S, vnew,
+                                                       keep, kept, tot, zero_sum);
+      });
+    } else {
+      // storage-free tier: the union in increasing id order, three passes
+      if (!summed)
+        for (int q = nb.q0; q < nb.q1; ++q) nb.dsum += __int_as_float(__ldg(nb.Lcv + LF_CK(nb, q, nb.L_nnz)).y);
+      const int2 ri = __ldg(nb.rows + i);
+      nb.p0 = ri.x;
+      nb.p1 = ri.x + ri.y;
+      float G, F;
+      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+        nb.sums(l, G, F);
+        if (in_skeleton(F, G)) add_to_sums(S, l == base, F, G, root(F));
+      }
+      const Update U(S, c);
+      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+        nb.sums(l, G, F);
+        if (in_skeleton(F, G)) tot += U.value(l == base, F, G, root(F), S, c);
+      }
+      if (!(tot > 0.0f)) zero_sum = true;
+      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+        nb.sums(l, G, F);
+        if (in_skeleton(F, G) &&
+            V::widen(V::round(__fmul_rn(U.value(l == base, F, G, root(F), S, c), 1.0f / tot))) != 0.0f)
+          ++kept;
+      }
+    }
+    nsk = S.nC + S.hasb;
+    if (zero_sum) kept = 0;
+  }
+
+  // ---- block scan of the output row lengths: offsets inside the segment ----
+  int x = kept;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  const unsigned sk = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(nsk));
+  if (lane == 31) {
+    s_warp_cnt[warp] = x;
+    s_red[warp] = sk;
+  }
+  const bool bad_sum = __syncthreads_or(zero_sum);
+  int warp_off = 0, tile_total = 0;
+  unsigned tile_sk = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    if (w < warp) warp_off += s_warp_cnt[w];
+    tile_total += s_warp_cnt[w];
+    tile_sk += s_red[w];
+  }
+  const int local_excl = warp_off + x - kept;
+
+  bool write = !bad_sum;
+  if (t == 0 && bad_sum) atomicOr(&st->err, ERR_ZERO_SUM);
+  if (write && tile_total > cap) {
+    write = false;
+    if (t == 0) {
+      atomicOr(&st->err, ERR_CAPACITY);
+      atomicMax(&st->need_tile, static_cast<unsigned long long>(tile_total));
+    }
+  }
+
+  // ---- write row i of the output, entries sorted by layer id ---------------
+  if (write && i < n_v) {
+    const int off = tile * cap + local_excl;
+    out.rows[i] = make_int2(off, kept);
+    T* ov = static_cast<T*>(out.vals);
+    int4 ho = make_int4(kept, 0, 0, 0);
+    auto put = [&](int o, int l, T vt) {
+#ifdef LF_CHECKED
+      const int w = tile * cap + nb.ck(o - tile * cap, cap);   // inside the tile's segment
+#else
+      const int w = o;
+#endif
+      out.ids[w] = static_cast<uint16_t>(l);
+      ov[w] = vt;
+      if (o == off) { ho.y = l; ho.z = V::bits(vt); }
+      else if (o == off + 1) { ho.y |= l << 16; ho.w = V::bits(vt); }
+    };
+    if (done0) {
+      int top = 1;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) top = keep[s] ? s + 1 : top;
+      with_slots4(__reduce_max_sync(__activemask(), top), [&](auto slots) {
+        slot_write<DT, decltype(slots)::value>(mp, keep, vnew, off, put);
+      });
+    } else {
+      const Update U(S, c);
+      float G, F;
+      int o = off;
+      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
+        nb.sums(l, G, F);
+        if (!in_skeleton(F, G)) continue;
+        const T vt = V::round(__fmul_rn(U.value(l == base, F, G, root(F), S, c), 1.0f / tot));
         if (V::widen(vt) != 0.0f) {
           put(o, l, vt);
           ++o;
@@ -1141,12 +1480,22 @@ using StepFn = void (*)(const BatchParams);
 const StepFn kStepFns[3][2] = {{&step_kernel_impl<0, false>, &step_kernel_impl<0, true>},
                                 {&step_kernel_impl<1, false>, &step_kernel_impl<1, true>},
                                 {&step_kernel_impl<2, false>, &step_kernel_impl<2, true>}};
+const StepFn kLeanFns[3] = {&step_kernel_lean<0>, &step_kernel_lean<1>, &step_kernel_lean<2>};
 
 }  // namespace
 
 int step_slots() { return kSlots; }
 
-const void* step_kernel(int dtype, bool general) { return reinterpret_cast<const void*>(kStepFns[dtype][general]); }
+// The kernel of a launch kind; jobs with coefficient matrices always take the
+// general-coefficient form of the full kernel.
+static StepFn step_fn(int kind, bool general) {
+  const int dtype = kind % 3;
+  const int sched = kind / 3;
+  if (general || sched == kSchedFull) return kStepFns[dtype][general];
+  return kLeanFns[dtype];
+}
+
+const void* step_kernel(int kind, bool general) { return reinterpret_cast<const void*>(step_fn(kind, general)); }
 
 bool needs_general(const BatchParams& p) {
   for (int j = 0; j < p.n_jobs; ++j)
@@ -1154,7 +1503,7 @@ bool needs_general(const BatchParams& p) {
   return false;
 }
 
-cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s) {
+cudaError_t launch_step(const BatchParams& p, int kind, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(p.tile_start[p.n_jobs]));
   cfg.blockDim = dim3(kBlock);
@@ -1165,7 +1514,7 @@ cudaError_t launch_step(const BatchParams& p, int dtype, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kStepFns[dtype][needs_general(p)], p);
+  return cudaLaunchKernelEx(&cfg, step_fn(kind, needs_general(p)), p);
 }
 
 #define LF_DISPATCH(dtype, KERNEL, GRID, BLOCK, STREAM, ...)                       \

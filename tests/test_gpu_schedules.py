@@ -1,0 +1,93 @@
+"""The two step-kernel schedules and the autotuner.
+
+Both schedules (the lean kernel: three-cell tier and storage-free tier; the
+full kernel: register map, shared-memory map, storage-free tier) must give
+the same bits on every job, alone and in batches that mix them; the
+autotuner (lf_tune) advances the job like lf_step while it times them.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lf():
+    import paper_1804_09152_gb300 as pkg
+    pkg.build()
+    from paper_1804_09152_gb300 import _lib
+    return _lib
+
+
+CASES = [
+    (lambda: synth.planar_grid(61, seed=2), 64, 3, "f32"),
+    (lambda: synth.noisy_torus(50), 48, 5, "bf16"),
+    (lambda: synth.icosphere(5), 3000, 9, "f32"),       # crowded: many rows of several cells
+    (lambda: synth.icosphere(3), 16, 1, "f16"),
+]
+
+
+def run(lf, m, k, sid, dt, schedule, steps=(3, 40, 300)):
+    out = []
+    with lf.Mesh(m.V, m.F, field_dtype=dt) as mesh:
+        mesh.set_schedule(schedule)
+        assert mesh.schedule == lf.SCHEDULES[schedule]
+        mesh.seed(synth.sample_seeds(m.n_v, k, sid))
+        for t in steps:
+            mesh.step(t)
+            out.append(mesh.get_field())
+        out.append((mesh.stats()["skeleton_total"], mesh.stats()["nnz_io_total"]))
+    return out
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_schedules_give_the_same_bits(lf, case):
+    fac, k, sid, dt = CASES[case]
+    m = fac()
+    a = run(lf, m, k, sid, dt, "lean")
+    b = run(lf, m, k, sid, dt, "full")
+    for fa, fb in zip(a[:-1], b[:-1]):
+        for x, y in zip(fa, fb):
+            assert np.array_equal(x, y)
+    assert a[-1] == b[-1]
+
+
+def test_batch_mixing_schedules_matches_alone(lf):
+    ms = [c[0]() for c in CASES[:3]]
+    alone = []
+    for (fac, k, sid, dt), m in zip(CASES[:3], ms):
+        alone.append(run(lf, m, k, sid, dt, "full", steps=(150,))[0])
+    meshes = []
+    for j, ((fac, k, sid, dt), m) in enumerate(zip(CASES[:3], ms)):
+        x = lf.Mesh(m.V, m.F, field_dtype=dt)
+        x.set_schedule(["lean", "full", "lean"][j])
+        x.seed(synth.sample_seeds(m.n_v, k, sid))
+        meshes.append(x)
+    lf.lf_step_batch(meshes, 150)
+    for x, want in zip(meshes, alone):
+        for p, q in zip(x.get_field(), want):
+            assert np.array_equal(p, q)
+        x.close()
+
+
+def test_tune_advances_the_job_and_keeps_a_schedule(lf):
+    m = synth.planar_grid(96, seed=9)
+    seeds = synth.sample_seeds(m.n_v, 80, 9)
+    with lf.Mesh(m.V, m.F) as a, lf.Mesh(m.V, m.F) as b:
+        a.seed(seeds)
+        b.seed(seeds)
+        s = a.tune(64)                     # two rounds over two schedules: 256 steps
+        assert s in (0, 1) and a.schedule == s
+        assert a.stats()["steps"] == 256
+        b.step(256)
+        for x, y in zip(a.get_field(), b.get_field()):
+            assert np.array_equal(x, y)
+        with pytest.raises(lf.LFError):
+            a.set_schedule(2)
+        with pytest.raises(lf.LFError):
+            a.tune(0)
+    with lf.Mesh(m.V, m.F) as c:
+        with pytest.raises(lf.LFError):
+            c.tune(16)                      # no field yet
