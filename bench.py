@@ -517,10 +517,14 @@ def run_batch(args):
         # faster (lf_tune); untimed, reported as tune_s
         torch.cuda.synchronize()
         t_tune = time.perf_counter()
-        for mesh, sd in zip(meshes, seeds):
-            mesh.seed(sd)
-            mesh.step(TUNE_AT)
-            mesh.tune(TUNE_TRIAL)
+        if args.schedule == "auto":
+            for mesh, sd in zip(meshes, seeds):
+                mesh.seed(sd)
+                mesh.step(TUNE_AT)
+                mesh.tune(TUNE_TRIAL)
+        else:
+            for mesh in meshes:
+                mesh.set_schedule(args.schedule)
         torch.cuda.synchronize()
         t_tune = time.perf_counter() - t_tune
         tuned = [mesh.schedule for mesh in meshes]
@@ -544,7 +548,7 @@ def run_batch(args):
             dist.barrier()
         # the same batch under one fixed schedule for every job
         fixed = {}
-        for name in ("lean", "full"):
+        for name in ("ctas4", "ctas5", "ctas3"):
             for mesh in meshes:
                 mesh.set_schedule(name)
             seed_all()
@@ -594,7 +598,7 @@ def run_batch(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": counters["bytes_per_step"] if counters else None, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_step": bytes_total / launches, "us_per_step": 1e6 * secs / launches,
-                "launches_per_step": len({sp.dtype for sp in specs})}
+                "launches_per_step": len({(sp.dtype, sc) for sp, sc in zip(specs, tuned)})}
     clk_summary = clk.summary()
     if counters:
         mhz = clk_summary.get("sm_mhz") or clk_summary.get("sm_max_mhz") or 2070.0
@@ -618,11 +622,13 @@ def run_batch(args):
                        "what": "one batch of 64 jobs, seeds to 1000 steps"},
         "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": (units / secs) / (units_plain / t_plain),
                      "desc": "the same jobs stepped one after another with lf_step on this GPU"},
-        "schedules": {"tuned": units / secs, "all_lean": fixed["lean"], "all_full": fixed["full"], "unit": UNIT,
-                      "jobs_lean": tuned.count(0), "jobs_full": tuned.count(1), "tune_s": t_tune,
+        "schedules": {("tuned" if args.schedule == "auto" else args.schedule): units / secs,
+                      **{f"all_{k}": v for k, v in fixed.items()}, "unit": UNIT,
+                      "jobs": {k: tuned.count(v) for k, v in lf.SCHEDULES.items()}, "tune_s": t_tune,
                       "desc": f"per job, lf_tune after {TUNE_AT} steps ({TUNE_TRIAL} steps per schedule and round, "
-                              "two rounds) picks the lean or the full step kernel (same bits); the batch under "
-                              "the tuned schedules against every job under one fixed schedule"},
+                              "two rounds) picks the step kernel's register allocation for 4, 5 or 3 CTAs per SM "
+                              "(same bits); the batch under the tuned schedules against every job under one "
+                              "fixed schedule"},
         "roofline": roofline,
         "e2e": {"value": e2e_units / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(24 * m.n_v + 12 * m.n_f + 4 * len(sd) for m, sd in zip(geo, seeds))),
@@ -897,6 +903,8 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=None,
                     help="time steps per job of one reference-arm step (default: 40, 3 for batch64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", choices=["auto", "ctas4", "ctas5", "ctas3"], default="auto",
+                    help="batch64: the step-kernel schedule of every job (auto: lf_tune per job)")
     args = ap.parse_args()
     batch = args.workload == "batch64"
     if args.cpu_sample_steps is None:

@@ -329,22 +329,22 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers,
 
 /*
  * Step-kernel schedules (no counterpart in the paper, which runs one mesh).
- * Two kernels advance a job with the same bits:
- *   0 (lean): a three-cell tier for vertices whose closed neighbourhood
- *     holds at most three cells, each row at most one cell and then the base
- *     layer (the steady state), and the storage-free tier for the rest --
- *     fast where that shape holds everywhere, slow wherever it does not;
- *   1 (full, the default): register-map, shared-memory and storage-free
- *     tiers.
- * Jobs with coefficient matrices always take the general form of the full
- * kernel.  lf_set_schedule fixes a job's schedule; lf_schedule reads it (-1
- * for NULL).  lf_tune is the autotuner: it runs trial_steps time-iterations
- * under each schedule twice (in alternating order), timed with CUDA events on
- * the mesh's stream, keeps the fastest for the job and returns it in
- * *schedule (nullable).  The trial steps advance the job like lf_step (they
- * count in its steps and statistics).  lf_step and lf_step_batch run each job
- * under its schedule; a batch launches once per step for every storage type
- * and schedule present.
+ * The step kernel is compiled three times, its registers allocated for 4
+ * (schedule 0, the default), 5 (schedule 1) and 3 (schedule 2) resident CTAs
+ * per SM (the FP32 kernel takes 62, 48 and 79 registers a thread).  All give the same bits; which is
+ * fastest depends on the job: more resident warps hide the gather's latency
+ * on large meshes, more registers per thread help small ones (measured on
+ * GB300 in steady state: a 1024^2 torus 83.1 / 84.4 / 93.4 us a step under
+ * schedules 1 / 0 / 2, a 150^2 torus 20.4 / 19.3 / 18.2 us).  Jobs with
+ * coefficient matrices always take the general-coefficient kernel at 4 CTAs.
+ * lf_set_schedule fixes a job's schedule; lf_schedule reads it (-1 for
+ * NULL).  lf_tune is the autotuner: it runs trial_steps time-iterations under
+ * each schedule twice (the second round in reverse order), timed with CUDA
+ * events on the mesh's stream, keeps the fastest for the job and returns it
+ * in *schedule (nullable).  The trial steps advance the job like lf_step
+ * (they count in its steps and statistics).  lf_step and lf_step_batch run
+ * each job under its schedule; a batch launches once per step for every
+ * storage type and schedule present.
  */
 lf_status lf_set_schedule(lf_mesh m, int32_t schedule);
 int32_t lf_schedule(lf_mesh m);

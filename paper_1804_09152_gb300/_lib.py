@@ -262,7 +262,7 @@ def lf_step(mesh, n_iters):
     _check(_lib.lf_step(mesh, int(n_iters)), mesh)
 
 
-SCHEDULES = {"lean": 0, "full": 1}
+SCHEDULES = {"ctas4": 0, "ctas5": 1, "ctas3": 2}    # the step kernel's resident CTAs per SM
 
 
 def lf_set_schedule(mesh, schedule):
@@ -411,7 +411,7 @@ class Mesh:
         lf_step(self.h, n)
 
     def set_schedule(self, schedule):
-        """0 / "lean" or 1 / "full" (the same bits either way)."""
+        """0 / "ctas4" (the default), 1 / "ctas5" or 2 / "ctas3": the same bits either way."""
         lf_set_schedule(self.h, schedule)
 
     @property

@@ -46,7 +46,7 @@ struct lf_mesh_s {
   int64_t n_v = 0;
   int64_t L_nnz = 0;
   int dtype = 0;
-  int sched = lf::kSchedFull;    // step-kernel schedule (lf_set_schedule, lf_tune)
+  int sched = lf::kSched4;       // step-kernel schedule (lf_set_schedule, lf_tune)
   int n_layers = 0;
   int num_tiles = 0;
   int64_t tile_cap = 0;          // entries per tile segment

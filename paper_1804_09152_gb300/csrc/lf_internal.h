@@ -110,11 +110,14 @@ int step_slots();
 // Kernel entry of the step for a storage type (0 f32, 1 bf16, 2 f16), in
 // the form for general coefficient matrices or not; its only argument is a
 // BatchParams.
-// Step-kernel schedules.  Both give the same bits; which is faster depends on
-// the job (how much of its neighbourhood the three-cell tier covers).
-constexpr int kSchedLean = 0;   // three-cell tier, storage-free tier for the rest
-constexpr int kSchedFull = 1;   // three-cell tier is not used: register map, shared-memory map, storage-free
-constexpr int kSchedules = 2;
+// Step-kernel schedules: the register allocation of the step kernel for 4,
+// 5 or 3 resident CTAs per SM (62, 48 and 79 registers a thread in FP32).  All give
+// the same bits; which is fastest depends on the job (its size against the
+// GPU, its degree and its cells).
+constexpr int kSched4 = 0;      // the default
+constexpr int kSched5 = 1;
+constexpr int kSched3 = 2;
+constexpr int kSchedules = 3;
 // A launch kind: the storage type and the schedule of the jobs in one launch.
 inline int step_kind(int dtype, int sched) { return dtype + 3 * sched; }
 const void* step_kernel(int kind, bool general);

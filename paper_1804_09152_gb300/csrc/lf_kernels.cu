@@ -89,8 +89,7 @@ constexpr int kBlock = kTile;   // threads (= vertices) per CTA
 #define LF_SLOTS 5
 #endif
 constexpr int kSlots = LF_SLOTS; // register map slots of the fast path
-constexpr int kChunk = 2;       // neighbours fetched per batch on the register-map tier
-constexpr int kChunk0 = 4;      // neighbours fetched per batch on the three-cell tier
+constexpr int kChunk = 2;       // neighbours fetched per batch
 constexpr int kPool = 4;        // medium-path maps per CTA
 constexpr int kMed = 32;        // slots of a medium-path map
 
@@ -412,20 +411,7 @@ struct MedMap {
 };
 
 
-// Runs fn with the number of register slots a warp's lanes use at most, for
-// the three-cell tier (three cells and the base layer at most).
-template <class Fn>
-__device__ __forceinline__ void with_slots4(int n, Fn&& fn) {
-  switch (n) {
-    case 1: fn(std::integral_constant<int, 1>{}); break;
-    case 2: fn(std::integral_constant<int, 2>{}); break;
-    case 3: fn(std::integral_constant<int, 3>{}); break;
-    default: fn(std::integral_constant<int, 4>{}); break;
-  }
-}
-
-// The update over a register map of N live slots, shared by the register-map
-// and three-cell tiers: the diagonal term of the own entries, ascending slot
+// The update over a register map of N live slots: the diagonal term of the own entries, ascending slot
 // order, the skeleton test, the per-vertex sums, Algorithm 1's update (the
 // class closed form or the general matrices), the clamp, the normalisation
 // and the rounding to the storage type.
@@ -519,8 +505,9 @@ __device__ __forceinline__ void slot_write(const SlotMap& mp, const bool (&keep)
 // ---------------------------------------------------------------------------
 enum : int { kFast = 0, kMedium = 1, kSlow = 2 };
 
-template <int DT, bool GEN>
-__global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_constant__ BatchParams P) {
+// MINB: CTAs per SM the register allocation is made for (the schedule).
+template <int DT, bool GEN, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_constant__ BatchParams P) {
   using V = Val<DT>;
   using T = typename V::T;
   constexpr int kWarps = kBlock / 32;
@@ -1056,310 +1043,6 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_impl(const __grid_const
 }
 
 // ---------------------------------------------------------------------------
-// the lean step kernel (class coefficients): the three-cell tier, and the
-// storage-free tier for every vertex outside it
-// ---------------------------------------------------------------------------
-// The same time-iteration as step_kernel_impl, for the steady-state shape
-// that nearly every vertex takes once the cells have formed: every row of the
-// closed neighbourhood holds at most one cell and then the base layer, and
-// the neighbourhood holds at most three cells.  Three cell sums and the base
-// sum are kept in registers; a neighbour's cell either matches a slot or
-// opens the next one, each sum taken in the order of the row of L exactly as
-// on the register-map tier.  A vertex outside the shape takes the
-// storage-free tier (the union in increasing id order by repeated minimum
-// search).  Every tier rounds every operation explicitly in the same order,
-// so the result is bit for bit that of step_kernel_impl; without the
-// register-map and shared-memory tiers the kernel is smaller, and it is the
-// faster of the two where the shape holds nearly everywhere.
-template <int DT>
-__global__ void __launch_bounds__(kBlock, 4) step_kernel_lean(const __grid_constant__ BatchParams P) {
-  using V = Val<DT>;
-  using T = typename V::T;
-  constexpr int kWarps = kBlock / 32;
-  __shared__ uint32_t s_err;
-  __shared__ unsigned s_red[kWarps];
-  __shared__ int s_warp_cnt[kWarps];
-
-  wait_previous_grid();
-  allow_next_grid();
-
-  int lo = 0, hi = P.n_jobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (P.tile_start[mid] <= static_cast<int>(blockIdx.x)) lo = mid; else hi = mid - 1;
-  }
-  const JobDesc& J = P.job[lo];
-  if (P.step >= J.steps) return;
-
-  const int t = threadIdx.x;
-  const int lane = t & 31;
-  const int warp = t >> 5;
-  const int tile = static_cast<int>(blockIdx.x) - P.tile_start[lo];
-  const int n_v = J.n_v;
-  const int base = J.n_layers - 1;
-  const int cap = J.tile_cap;
-  const int par = (J.parity0 + P.step) & 1;
-  const FieldBuf in = J.buf[par];
-  const FieldBuf out = J.buf[par ^ 1];
-  const Coefs& c = J.c;
-  DevStatus* st = J.st;
-
-  Neighbourhood<DT> nb;
-  nb.rows = in.rows;
-  nb.Fid = in.ids;
-  nb.Fval = static_cast<const T*>(in.vals);
-  nb.Lcv = J.L_colval;
-  nb.dsum = 0.0f;
-  nb.p0 = nb.p1 = nb.q0 = nb.q1 = 0;
-#ifdef LF_CHECKED
-  nb.st = J.st;
-  nb.n_v = J.n_v;
-  nb.L_nnz = J.L_nnz;
-  nb.entries = J.num_tiles * J.tile_cap;
-#endif
-
-  const int i = tile * kBlock + t;
-  int4 h_own = make_int4(0, 0, 0, 0);
-  if (i < n_v) {
-    h_own = __ldg(in.head + i);
-    nb.q0 = __ldg(J.L_rowptr + i);
-    nb.q1 = __ldg(J.L_rowptr + i + 1);
-  }
-  if (t == 0) s_err = ld_relaxed_u32(&st->err);
-  __syncthreads();
-  if (s_err) return;                 // an earlier step of this job failed
-
-  SlotMap mp;
-  mp.clear();
-  bool zero_sum = false;
-  int kept = 0, nsk = 0;
-  const int own = h_own.x;
-  float vnew[kSlots];
-  bool keep[kSlots];
-#pragma unroll
-  for (int s = 0; s < kSlots; ++s) { vnew[s] = 0.0f; keep[s] = false; }
-  VertexSums S = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, 0};
-  float tot = 0.0f;
-  int own_cells = own;
-  bool done0 = false;
-  bool summed = false;               // nb.dsum holds the row sum of L
-  {
-    const int e0o = h_own.y & 0xffff;
-    const int e1o = (h_own.y >> 16) & 0xffff;
-    const bool own_simple = i < n_v && own <= 2 && (own < 2 || e1o == base);
-    if (__any_sync(0xffffffffu, own_simple) && own_simple) {
-      int c0 = -1, c1 = -1, c2 = -1;
-      float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, gb = 0.0f, ds = 0.0f, f0 = 0.0f, fb = 0.0f;
-      int ownc = 0;
-      if (own >= 1) {
-        if (e0o == base) {
-          fb = V::from_bits(h_own.z);
-        } else {
-          c0 = e0o;
-          f0 = V::from_bits(h_own.z);
-          ownc = 1;
-        }
-      }
-      if (own == 2) fb = V::from_bits(h_own.w);
-      bool ok = true;
-      for (int qb = nb.q0; qb < nb.q1; qb += kChunk0) {
-        int2 cv[kChunk0];
-#pragma unroll
-        for (int k = 0; k < kChunk0; ++k) {
-          cv[k] = make_int2(-1, 0);
-          if (qb + k < nb.q1) cv[k] = __ldg(nb.Lcv + LF_CK(nb, qb + k, nb.L_nnz));
-        }
-        int4 hj[kChunk0];
-#pragma unroll
-        for (int k = 0; k < kChunk0; ++k) {
-          hj[k] = make_int4(0, 0, 0, 0);
-          if (cv[k].x >= 0) hj[k] = __ldg(in.head + LF_CK(nb, cv[k].x, nb.n_v));
-        }
-#pragma unroll
-        for (int k = 0; k < kChunk0; ++k) {
-          if (cv[k].x < 0) continue;
-          const float lij = __int_as_float(cv[k].y);
-          ds += lij;
-          const int rn = hj[k].x;
-          const int e0 = hj[k].y & 0xffff;
-          const int e1 = (hj[k].y >> 16) & 0xffff;
-          ok = ok && rn <= 2 && (rn < 2 || e1 == base);
-          const float x0 = __fmul_rn(lij, V::from_bits(hj[k].z));
-          const float x1 = __fmul_rn(lij, V::from_bits(hj[k].w));
-          // the base entry: the only entry, or the second one
-          const bool b0 = rn >= 1 && e0 == base;
-          gb = b0 ? __fadd_rn(gb, x0) : gb;
-          gb = (rn == 2 && e1 == base) ? __fadd_rn(gb, x1) : gb;
-          // the cell entry: the first one, unless it is the base
-          const int cell = (rn >= 1 && !b0) ? e0 : -2;
-          const bool m0 = cell == c0, m1 = cell == c1, m2 = cell == c2;
-          const bool fresh = cell >= 0 && !m0 && !m1 && !m2;
-          const bool o0 = fresh && c0 < 0;
-          const bool o1 = fresh && c0 >= 0 && c1 < 0;
-          const bool o2 = fresh && c1 >= 0 && c2 < 0;
-          ok = ok && !(fresh && c2 >= 0);
-          g0 = o0 ? x0 : (m0 ? __fadd_rn(g0, x0) : g0);
-          g1 = o1 ? x0 : (m1 ? __fadd_rn(g1, x0) : g1);
-          g2 = o2 ? x0 : (m2 ? __fadd_rn(g2, x0) : g2);
-          c0 = o0 ? cell : c0;
-          c1 = o1 ? cell : c1;
-          c2 = o2 ? cell : c2;
-        }
-      }
-      nb.dsum = ds;                  // the whole row was read either way
-      summed = true;
-      if (ok) {
-        done0 = true;
-        own_cells = ownc;
-        mp.id[0] = c0; mp.g[0] = g0; mp.f[0] = f0;
-        mp.id[1] = c1; mp.g[1] = g1;
-        mp.id[2] = c2; mp.g[2] = g2;
-        const int ncell = (c0 >= 0) + (c1 >= 0) + (c2 >= 0);
-        // the base layer joins the slots last (largest id)
-#pragma unroll
-        for (int s2 = 0; s2 < kSlots; ++s2) {
-          if (s2 == ncell) { mp.id[s2] = base; mp.g[s2] = gb; mp.f[s2] = fb; }
-        }
-        mp.cnt = ncell + 1;
-      }
-    }
-  }
-
-  const GenCoef gc{};                // unused: class coefficients only
-  if (i < n_v) {
-    if (done0) {
-      with_slots4(__reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
-        slot_update<DT, false, decltype(slots)::value>(mp, own_cells, own, nb.dsum, base, c, gc, false, S, vnew,
-                                                       keep, kept, tot, zero_sum);
-      });
-    } else {
-      // storage-free tier: the union in increasing id order, three passes
-      if (!summed)
-        for (int q = nb.q0; q < nb.q1; ++q) nb.dsum += __int_as_float(__ldg(nb.Lcv + LF_CK(nb, q, nb.L_nnz)).y);
-      const int2 ri = __ldg(nb.rows + i);
-      nb.p0 = ri.x;
-      nb.p1 = ri.x + ri.y;
-      float G, F;
-      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
-        nb.sums(l, G, F);
-        if (in_skeleton(F, G)) add_to_sums(S, l == base, F, G, root(F));
-      }
-      const Update U(S, c);
-      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
-        nb.sums(l, G, F);
-        if (in_skeleton(F, G)) tot += U.value(l == base, F, G, root(F), S, c);
-      }
-      if (!(tot > 0.0f)) zero_sum = true;
-      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
-        nb.sums(l, G, F);
-        if (in_skeleton(F, G) &&
-            V::widen(V::round(__fmul_rn(U.value(l == base, F, G, root(F), S, c), 1.0f / tot))) != 0.0f)
-          ++kept;
-      }
-    }
-    nsk = S.nC + S.hasb;
-    if (zero_sum) kept = 0;
-  }
-
-  // ---- block scan of the output row lengths: offsets inside the segment ----
-  int x = kept;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  const unsigned sk = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(nsk));
-  if (lane == 31) {
-    s_warp_cnt[warp] = x;
-    s_red[warp] = sk;
-  }
-  const bool bad_sum = __syncthreads_or(zero_sum);
-  int warp_off = 0, tile_total = 0;
-  unsigned tile_sk = 0;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    if (w < warp) warp_off += s_warp_cnt[w];
-    tile_total += s_warp_cnt[w];
-    tile_sk += s_red[w];
-  }
-  const int local_excl = warp_off + x - kept;
-
-  bool write = !bad_sum;
-  if (t == 0 && bad_sum) atomicOr(&st->err, ERR_ZERO_SUM);
-  if (write && tile_total > cap) {
-    write = false;
-    if (t == 0) {
-      atomicOr(&st->err, ERR_CAPACITY);
-      atomicMax(&st->need_tile, static_cast<unsigned long long>(tile_total));
-    }
-  }
-
-  // ---- write row i of the output, entries sorted by layer id ---------------
-  if (write && i < n_v) {
-    const int off = tile * cap + local_excl;
-    out.rows[i] = make_int2(off, kept);
-    T* ov = static_cast<T*>(out.vals);
-    int4 ho = make_int4(kept, 0, 0, 0);
-    auto put = [&](int o, int l, T vt) {
-#ifdef LF_CHECKED
-      const int w = tile * cap + nb.ck(o - tile * cap, cap);   // inside the tile's segment
-#else
-      const int w = o;
-#endif
-      out.ids[w] = static_cast<uint16_t>(l);
-      ov[w] = vt;
-      if (o == off) { ho.y = l; ho.z = V::bits(vt); }
-      else if (o == off + 1) { ho.y |= l << 16; ho.w = V::bits(vt); }
-    };
-    if (done0) {
-      int top = 1;
-#pragma unroll
-      for (int s = 0; s < kSlots; ++s) top = keep[s] ? s + 1 : top;
-      with_slots4(__reduce_max_sync(__activemask(), top), [&](auto slots) {
-        slot_write<DT, decltype(slots)::value>(mp, keep, vnew, off, put);
-      });
-    } else {
-      const Update U(S, c);
-      float G, F;
-      int o = off;
-      for (int l = nb.next_layer(-1); l != 0x7fffffff; l = nb.next_layer(l)) {
-        nb.sums(l, G, F);
-        if (!in_skeleton(F, G)) continue;
-        const T vt = V::round(__fmul_rn(U.value(l == base, F, G, root(F), S, c), 1.0f / tot));
-        if (V::widen(vt) != 0.0f) {
-          put(o, l, vt);
-          ++o;
-        }
-      }
-    }
-    out.head[i] = ho;
-  }
-
-  // ---- end of step: the last CTA of the job commits the step ----------------
-  if (t == 0) {
-    atomicAdd(&st->skeleton_step, static_cast<unsigned long long>(tile_sk));
-    atomicAdd(&st->nnz_step, static_cast<unsigned long long>(tile_total));
-    __threadfence();
-    const uint32_t prev = atomicAdd(&st->done, 1u);
-    if (prev == static_cast<uint32_t>(J.num_tiles) - 1u) {
-      __threadfence();
-      if (ld_relaxed_u32(&st->err) == 0u) {
-        const unsigned long long nin = ld_relaxed(&st->nnz);
-        const unsigned long long nout = ld_relaxed(&st->nnz_step);
-        st->skeleton_total = ld_relaxed(&st->skeleton_total) + ld_relaxed(&st->skeleton_step);
-        st->nnz_io_total = ld_relaxed(&st->nnz_io_total) + nin + nout;
-        st->nnz = nout;
-        st->epoch = st->epoch + 1u;
-      }
-      st->skeleton_step = 0ull;
-      st->nnz_step = 0ull;
-      st->done = 0u;
-      __threadfence();
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // seeding, labels, relayout, conversions
 // ---------------------------------------------------------------------------
 template <int DT>
@@ -1477,22 +1160,25 @@ __global__ void narrow_kernel(const float* __restrict__ src, void* __restrict__ 
 }
 
 using StepFn = void (*)(const BatchParams);
-const StepFn kStepFns[3][2] = {{&step_kernel_impl<0, false>, &step_kernel_impl<0, true>},
-                                {&step_kernel_impl<1, false>, &step_kernel_impl<1, true>},
-                                {&step_kernel_impl<2, false>, &step_kernel_impl<2, true>}};
-const StepFn kLeanFns[3] = {&step_kernel_lean<0>, &step_kernel_lean<1>, &step_kernel_lean<2>};
+// [schedule][storage type]: the class-coefficient kernel at 4, 5 and 3 CTAs
+// per SM; the general-coefficient form keeps 4.
+const StepFn kClassFns[kSchedules][3] = {
+    {&step_kernel_impl<0, false, 4>, &step_kernel_impl<1, false, 4>, &step_kernel_impl<2, false, 4>},
+    {&step_kernel_impl<0, false, 5>, &step_kernel_impl<1, false, 5>, &step_kernel_impl<2, false, 5>},
+    {&step_kernel_impl<0, false, 3>, &step_kernel_impl<1, false, 3>, &step_kernel_impl<2, false, 3>}};
+const StepFn kGeneralFns[3] = {&step_kernel_impl<0, true, 4>, &step_kernel_impl<1, true, 4>,
+                               &step_kernel_impl<2, true, 4>};
 
 }  // namespace
 
 int step_slots() { return kSlots; }
 
-// The kernel of a launch kind; jobs with coefficient matrices always take the
-// general-coefficient form of the full kernel.
+// The kernel of a launch kind; a launch with coefficient matrices takes the
+// general-coefficient form.
 static StepFn step_fn(int kind, bool general) {
   const int dtype = kind % 3;
   const int sched = kind / 3;
-  if (general || sched == kSchedFull) return kStepFns[dtype][general];
-  return kLeanFns[dtype];
+  return general ? kGeneralFns[dtype] : kClassFns[sched][dtype];
 }
 
 const void* step_kernel(int kind, bool general) { return reinterpret_cast<const void*>(step_fn(kind, general)); }

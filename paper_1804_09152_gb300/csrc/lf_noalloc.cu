@@ -137,7 +137,7 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers, cons
 
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaMemcpyAsync(&d_layout->st, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = lf::launch_step(bp, lf::step_kind(LF_F32, lf::kSchedFull), stream);
+  if (e == cudaSuccess) e = lf::launch_step(bp, lf::step_kind(LF_F32, lf::kSched4), stream);
   lf::DevStatus st;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&st, &d_layout->st, sizeof(st), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

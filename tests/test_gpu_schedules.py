@@ -1,9 +1,9 @@
-"""The two step-kernel schedules and the autotuner.
+"""The step-kernel schedules and the autotuner.
 
-Both schedules (the lean kernel: three-cell tier and storage-free tier; the
-full kernel: register map, shared-memory map, storage-free tier) must give
-the same bits on every job, alone and in batches that mix them; the
-autotuner (lf_tune) advances the job like lf_step while it times them.
+The three schedules (the step kernel's registers allocated for 4, 5 and 3
+resident CTAs per SM) must give the same bits on every job, alone and in
+batches that mix them; the autotuner (lf_tune) advances the job like
+lf_step while it times them.
 """
 import numpy as np
 import pytest
@@ -46,23 +46,24 @@ def run(lf, m, k, sid, dt, schedule, steps=(3, 40, 300)):
 def test_schedules_give_the_same_bits(lf, case):
     fac, k, sid, dt = CASES[case]
     m = fac()
-    a = run(lf, m, k, sid, dt, "lean")
-    b = run(lf, m, k, sid, dt, "full")
-    for fa, fb in zip(a[:-1], b[:-1]):
-        for x, y in zip(fa, fb):
-            assert np.array_equal(x, y)
-    assert a[-1] == b[-1]
+    a = run(lf, m, k, sid, dt, "ctas4")
+    for other in ("ctas5", "ctas3"):
+        b = run(lf, m, k, sid, dt, other)
+        for fa, fb in zip(a[:-1], b[:-1]):
+            for x, y in zip(fa, fb):
+                assert np.array_equal(x, y)
+        assert a[-1] == b[-1]
 
 
 def test_batch_mixing_schedules_matches_alone(lf):
     ms = [c[0]() for c in CASES[:3]]
     alone = []
     for (fac, k, sid, dt), m in zip(CASES[:3], ms):
-        alone.append(run(lf, m, k, sid, dt, "full", steps=(150,))[0])
+        alone.append(run(lf, m, k, sid, dt, "ctas4", steps=(150,))[0])
     meshes = []
     for j, ((fac, k, sid, dt), m) in enumerate(zip(CASES[:3], ms)):
         x = lf.Mesh(m.V, m.F, field_dtype=dt)
-        x.set_schedule(["lean", "full", "lean"][j])
+        x.set_schedule(["ctas5", "ctas4", "ctas3"][j])
         x.seed(synth.sample_seeds(m.n_v, k, sid))
         meshes.append(x)
     lf.lf_step_batch(meshes, 150)
@@ -78,14 +79,14 @@ def test_tune_advances_the_job_and_keeps_a_schedule(lf):
     with lf.Mesh(m.V, m.F) as a, lf.Mesh(m.V, m.F) as b:
         a.seed(seeds)
         b.seed(seeds)
-        s = a.tune(64)                     # two rounds over two schedules: 256 steps
-        assert s in (0, 1) and a.schedule == s
-        assert a.stats()["steps"] == 256
-        b.step(256)
+        s = a.tune(64)                     # two rounds over three schedules: 384 steps
+        assert s in (0, 1, 2) and a.schedule == s
+        assert a.stats()["steps"] == 384
+        b.step(384)
         for x, y in zip(a.get_field(), b.get_field()):
             assert np.array_equal(x, y)
         with pytest.raises(lf.LFError):
-            a.set_schedule(2)
+            a.set_schedule(3)
         with pytest.raises(lf.LFError):
             a.tune(0)
     with lf.Mesh(m.V, m.F) as c:
