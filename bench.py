@@ -101,11 +101,15 @@ WORKLOADS = {
                  mesh=lambda: synth.icosphere(3), k=16, seed_stream=1, steps=300, dtype="f32"),
 }
 
-# Counters of one step-kernel launch from an ncu capture of the grid512
-# workload (FP32 field, steady state): DRAM bytes and warp instructions.
-# Valid only for that workload and the kernel source they were taken on.
-NCU_COUNTERS = {"grid512": {"dtype": "f32", "kernel_sha": "b677234052a5a212",
-                             "bytes_per_launch": 17869056, "warp_instructions_per_launch": 11762763}}
+# Counters of the step kernel from ncu captures (DRAM bytes and warp
+# instructions; steady state), valid only for the workload and the kernel
+# source they were taken on.
+NCU_COUNTERS = {"grid512": {"dtype": "f32", "kernel_sha": "f837f2781cf092bd",
+                             "bytes_per_launch": 17870080, "warp_instructions_per_launch": 11762763},
+                # one step of the batch with every job on schedule ctas4 (its FP32 and BF16
+                # launches, steps ~500 of 1000): DRAM read + write bytes and warp instructions
+                "batch64": {"kernel_sha": "f837f2781cf092bd", "measured_under": "every job on ctas4",
+                            "bytes_per_step": 956433408, "warp_instructions_per_step": 441048122}}
 SM_COUNT, SUBPARTITIONS = 152, 4          # GB300: 152 SMs, 4 schedulers each issuing one warp instruction a cycle
 L2_FLUSH_BYTES = 512 << 20
 
@@ -599,6 +603,8 @@ def run_batch(args):
                 "traffic": counters["bytes_per_step"] if counters else None, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_step": bytes_total / launches, "us_per_step": 1e6 * secs / launches,
                 "launches_per_step": len({(sp.dtype, sc) for sp, sc in zip(specs, tuned)})}
+    if counters:
+        roofline["traffic_measured_under"] = counters["measured_under"]
     clk_summary = clk.summary()
     if counters:
         mhz = clk_summary.get("sm_mhz") or clk_summary.get("sm_max_mhz") or 2070.0
