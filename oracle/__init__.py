@@ -57,7 +57,7 @@ def build(force=False):
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"])
+                               "-shared", "-fPIC", "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -257,9 +257,10 @@ def step(L, F, params=None, W=None, A=None, E=None, margins=False, threads=1):
     sk = np.zeros(1, np.int64)
     mg = np.zeros((F.n_v, 3), np.float64) if margins else None
     while True:
-        rp = np.zeros(F.n_v + 1, np.int64)
-        ids = np.zeros(cap, np.int32)
-        vals = np.zeros(cap, np.float64)
+        # written in full up to the returned count by the C side
+        rp = np.empty(F.n_v + 1, np.int64)
+        ids = np.empty(cap, np.int32)
+        vals = np.empty(cap, np.float64)
         args = (F.n_v, n, _p(L.rowptr), _p(L.col), _p(L.val),
                 _p(F.rowptr), _p(F.ids), _p(F.vals), _p(co), _p(Wm), _p(Am), _p(Em),
                 cap, _p(rp), _p(ids), _p(vals), _p(sk), _p(mg))

@@ -20,13 +20,11 @@
  * Each function cites the passage it follows.  Readings of passages that are
  * silent or ambiguous are marked READING.
  */
-#define _POSIX_C_SOURCE 200809L   /* sysconf, threads */
 #include <math.h>
-#include <pthread.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
-#include <unistd.h>
 
 #define ORC_OK 0
 #define ORC_ERR_INVALID (-1)
@@ -478,13 +476,14 @@ done:
 }
 
 /*
- * The same time-iteration computed by several threads (the timed CPU
+ * The same time-iteration computed by several OpenMP threads (the timed CPU
  * baseline): each thread takes a contiguous range of vertices and runs
  * steps (1)-(5) for one vertex at a time with the helpers of orc_step, so
  * every vertex gets the same operations in the same order and the result is
  * identical to orc_step's.  Every vertex's work reads only the input, so the
  * threads need no locks; each keeps its output rows in a buffer of its own,
- * and a prefix sum of the per-thread counts places them in the output.
+ * and a prefix sum of the per-thread counts places them in the output,
+ * where every thread copies its own rows.
  * n_threads <= 0 uses every online core.  Same outputs and return codes as
  * orc_step.
  */
@@ -562,20 +561,21 @@ int64_t orc_step_threads(int32_t n_threads, int64_t n_v, int32_t n_layers,
                          int64_t out_cap, int64_t* Orp, int32_t* Oid, double* Oval,
                          int64_t* skeleton, double* margins) {
   const orc_coefs c = unpack(coefs);
-  if (n_threads <= 0) {
-    long nc = sysconf(_SC_NPROCESSORS_ONLN);
-    n_threads = nc > 0 ? (int32_t)nc : 1;
-  }
+  if (n_threads <= 0) n_threads = omp_get_num_procs();
   if (n_threads > n_v) n_threads = n_v > 0 ? (int32_t)n_v : 1;
   mt_task* tasks = (mt_task*)calloc((size_t)n_threads, sizeof(mt_task));
-  pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
-  char* running = (char*)calloc((size_t)n_threads, 1);
   int64_t* counts = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_v > 0 ? n_v : 1));
-  if (!tasks || !th || !running || !counts) { free(tasks); free(th); free(running); free(counts); return ORC_ERR_NOMEM; }
-  for (int32_t k = 0; k < n_threads; ++k) {
+  int64_t* offs = (int64_t*)calloc((size_t)n_threads + 1, sizeof(int64_t));
+  if (!tasks || !counts || !offs) { free(tasks); free(counts); free(offs); return ORC_ERR_NOMEM; }
+  int64_t ret = 0, nnz = 0, skel = 0;
+  int nt_used = 1;
+#pragma omp parallel num_threads(n_threads)
+  {
+    const int k = omp_get_thread_num();
+    const int nt = omp_get_num_threads();
     mt_task* t = &tasks[k];
-    t->lo = n_v * k / n_threads;
-    t->hi = n_v * (k + 1) / n_threads;
+    t->lo = n_v * k / nt;
+    t->hi = n_v * (k + 1) / nt;
     t->n_layers = n_layers;
     t->Lrp = Lrp; t->Lcol = Lcol; t->Lval = Lval;
     t->Frp = Frp; t->Fid = Fid; t->Fval = Fval;
@@ -583,35 +583,37 @@ int64_t orc_step_threads(int32_t n_threads, int64_t n_v, int32_t n_layers,
     t->c = &c;
     t->margins = margins;
     t->counts = counts;
-    t->err = ORC_ERR_NOMEM;
-    if (k > 0) running[k] = pthread_create(&th[k], NULL, mt_worker, t) == 0;
-  }
-  for (int32_t k = 0; k < n_threads; ++k)
-    if (!running[k]) mt_worker(&tasks[k]);     /* the calling thread, and any thread not to be had */
-  for (int32_t k = 1; k < n_threads; ++k)
-    if (running[k]) pthread_join(th[k], NULL);
-  int64_t ret = 0, nnz = 0, skel = 0;
-  for (int32_t k = 0; k < n_threads; ++k) {
-    if (tasks[k].err != ORC_OK && ret == 0) ret = tasks[k].err;
-    nnz += tasks[k].n_out;
-    skel += tasks[k].skel;
-  }
-  if (ret == 0 && nnz > out_cap) ret = -nnz - 16;
-  if (ret == 0) {
-    /* prefix sum of the per-thread counts: each thread's rows in place */
-    int64_t o = 0;
-    for (int32_t k = 0; k < n_threads; ++k) {
-      memcpy(Oid + o, tasks[k].oid, sizeof(int32_t) * (size_t)tasks[k].n_out);
-      memcpy(Oval + o, tasks[k].oval, sizeof(double) * (size_t)tasks[k].n_out);
-      o += tasks[k].n_out;
+    mt_worker(t);
+#pragma omp barrier
+#pragma omp single
+    {
+      /* prefix sum of the per-thread counts: each thread's rows in place */
+      nt_used = nt;
+      for (int x = 0; x < nt; ++x) {
+        if (tasks[x].err != ORC_OK && ret == 0) ret = tasks[x].err;
+        offs[x + 1] = offs[x] + tasks[x].n_out;
+        skel += tasks[x].skel;
+      }
+      nnz = offs[nt];
+      if (ret == 0 && nnz > out_cap) ret = -nnz - 16;
     }
-    Orp[0] = 0;
-    for (int64_t i = 0; i < n_v; ++i) Orp[i + 1] = Orp[i] + counts[i];
+    if (ret == 0) {
+      memcpy(Oid + offs[k], t->oid, sizeof(int32_t) * (size_t)t->n_out);
+      memcpy(Oval + offs[k], t->oval, sizeof(double) * (size_t)t->n_out);
+      int64_t o = offs[k];
+      if (k == 0) Orp[0] = 0;
+      for (int64_t i = t->lo; i < t->hi; ++i) {
+        o += counts[i];
+        Orp[i + 1] = o;
+      }
+    }
+  }
+  if (ret == 0) {
     if (skeleton) *skeleton = skel;
     ret = nnz;
   }
-  for (int32_t k = 0; k < n_threads; ++k) { free(tasks[k].oid); free(tasks[k].oval); }
-  free(tasks); free(th); free(running); free(counts);
+  for (int32_t x = 0; x < nt_used && x < n_threads; ++x) { free(tasks[x].oid); free(tasks[x].oval); }
+  free(tasks); free(counts); free(offs);
   return ret;
 }
 
