@@ -145,6 +145,9 @@ def test_mesh_calls_reject_a_null_handle_without_gpu(lib):
     lay = np.array([0], np.int32)
     val = np.array([1.0], np.float32)
     assert L.lf_set_field(None, lib._ptr(rp), lib._ptr(lay), lib._ptr(val), 1, 2) == lib.LF_ERR_INVALID
+    assert L.lf_set_schedule(None, 0) == lib.LF_ERR_INVALID
+    assert L.lf_schedule(None) == -1
+    assert L.lf_tune(None, 8, None) == lib.LF_ERR_INVALID
     L.lf_destroy_mesh(None)                    # a no-op
 
 
