@@ -256,13 +256,26 @@ def single_mesh_jobs(wl):
     return [(m, synth.sample_seeds(m.n_v, wl["k"], wl["seed_stream"]), mats)]
 
 
-def batch_jobs(specs=None):
+# Vertex order of the batch's meshes as given to the library: "generated"
+# (the generators' own: subdivision order for icospheres, scan order for
+# tori) or "locality" (renumbered by paper_1804_09152_gb300.ordering, as a
+# caller does with a scattered mesh: a Morton curve for icospheres, reverse
+# Cuthill-McKee for tori).
+BATCH_ORDER = {"ico": "morton", "torus": "rcm"}
+
+
+def batch_jobs(specs=None, order="generated"):
     specs = specs or synth.batch_mix()
     cache, jobs = {}, []
     for sp in specs:
         key = (sp.kind, sp.size)
         if key not in cache:
-            cache[key] = synth.make_mesh(sp)
+            m = synth.make_mesh(sp)
+            if order == "locality" and sp.kind in BATCH_ORDER:
+                from paper_1804_09152_gb300.ordering import locality_order
+                V, F, _ = locality_order(m.V, m.F, BATCH_ORDER[sp.kind])
+                m = synth.Mesh(V, F)
+            cache[key] = m
         m = cache[key]
         jobs.append((m, synth.sample_seeds(m.n_v, min(sp.k, m.n_v // 4), sp.seed_stream), None))
     return jobs
@@ -494,7 +507,7 @@ def run_batch(args):
     T = specs[0].steps
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    jobs = batch_jobs(specs)
+    jobs = batch_jobs(specs, args.order)
     geo = [m for m, _, _ in jobs]
     seeds = [sd for _, sd, _ in jobs]
     with torch.cuda.stream(stream):
@@ -619,7 +632,9 @@ def run_batch(args):
               "desc": "64 jobs: icosphere level 4-8 or noisy torus (p=1/2), n_v log-uniform 10k-600k, "
                       "k log-uniform 32-2048, FP32 or BF16 storage with FP32 arithmetic (p=1/2), "
                       "1000 steps (stream 6); a bench step is the whole batch",
-              "l2": "flushed before every timed batch (512 MiB write); the batch working set exceeds L2"}
+              "l2": "flushed before every timed batch (512 MiB write); the batch working set exceeds L2",
+              "vertex_order": args.order if args.order == "generated" else
+              "locality: icospheres along a Morton curve, tori by reverse Cuthill-McKee (ordering.locality_order)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -909,6 +924,8 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=None,
                     help="time steps per job of one reference-arm step (default: 40, 3 for batch64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--order", choices=["generated", "locality"], default="generated",
+                    help="batch64: the meshes' vertex numbering (locality: renumbered before lf_create_mesh)")
     ap.add_argument("--schedule", choices=["auto", "ctas4", "ctas5", "ctas3"], default="auto",
                     help="batch64: the step-kernel schedule of every job (auto: lf_tune per job)")
     args = ap.parse_args()
@@ -924,7 +941,7 @@ def main():
         config = {"workload": "batch64", "jobs": len(specs), "time_steps_per_job": specs[0].steps,
                   "desc": "64 jobs: icosphere level 4-8 or noisy torus (p=1/2), n_v log-uniform 10k-600k, "
                           "k log-uniform 32-2048, 1000 steps (stream 6); the oracle computes in FP64"}
-        return run_reference(args, batch_jobs(specs), config, args.ref_sample_steps)
+        return run_reference(args, batch_jobs(specs, args.order), config, args.ref_sample_steps)
     if args.impl == "reference" and args.workload not in WORKLOADS:
         if int(os.environ.get("RANK", "0")) == 0:
             print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times the batch and the "
