@@ -565,7 +565,7 @@ def run_batch(args):
             dist.barrier()
         # the same batch under one fixed schedule for every job
         fixed = {}
-        for name in ("ctas4", "ctas5", "ctas3"):
+        for name in (() if args.timed_only else ("ctas4", "ctas5", "ctas3", "hot", "lean")):
             for mesh in meshes:
                 mesh.set_schedule(name)
             seed_all()
@@ -575,28 +575,30 @@ def run_batch(args):
             fixed[name] = sum(mesh.stats()["skeleton_total"] for mesh in meshes) / t_fixed
         for mesh, sc in zip(meshes, tuned):
             mesh.set_schedule(sc)
-        # the same jobs one at a time (each under its tuned schedule)
-        seed_all()
-        t_plain = timed(lambda: [mesh.step(T) for mesh in meshes])
-        units_plain = sum(mesh.stats()["skeleton_total"] for mesh in meshes)
-        # end to end through the C ABI from pinned host buffers: create (mesh
-        # upload, device operator build), seed, the batch, labels to the host
-        pinned = [(torch.from_numpy(np.ascontiguousarray(m.V)).pin_memory().numpy(),
-                   torch.from_numpy(np.ascontiguousarray(m.F)).pin_memory().numpy()) for m in geo]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        fresh = [lf.Mesh(V, F, device=dev, field_dtype=sp.dtype) for (V, F), sp in zip(pinned, specs)]
-        for mesh, sd, sc in zip(fresh, seeds, tuned):
-            mesh.set_schedule(sc)                   # the tuned schedule, as a serving process keeps it
-            mesh.seed(sd)
-        lf.lf_step_batch(fresh, T)
-        e2e_units = 0
-        for mesh in fresh:
-            mesh.labels()
-            e2e_units += mesh.stats()["skeleton_total"]
-            mesh.close()
-        torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
+        t_plain = units_plain = t_e2e = e2e_units = None
+        if not args.timed_only:
+            # the same jobs one at a time (each under its tuned schedule)
+            seed_all()
+            t_plain = timed(lambda: [mesh.step(T) for mesh in meshes])
+            units_plain = sum(mesh.stats()["skeleton_total"] for mesh in meshes)
+            # end to end through the C ABI from pinned host buffers: create (mesh
+            # upload, device operator build), seed, the batch, labels to the host
+            pinned = [(torch.from_numpy(np.ascontiguousarray(m.V)).pin_memory().numpy(),
+                       torch.from_numpy(np.ascontiguousarray(m.F)).pin_memory().numpy()) for m in geo]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fresh = [lf.Mesh(V, F, device=dev, field_dtype=sp.dtype) for (V, F), sp in zip(pinned, specs)]
+            for mesh, sd, sc in zip(fresh, seeds, tuned):
+                mesh.set_schedule(sc)                   # the tuned schedule, as a serving process keeps it
+                mesh.seed(sd)
+            lf.lf_step_batch(fresh, T)
+            e2e_units = 0
+            for mesh in fresh:
+                mesh.labels()
+                e2e_units += mesh.stats()["skeleton_total"]
+                mesh.close()
+            torch.cuda.synchronize()
+            t_e2e = time.perf_counter() - t0
         sts = [mesh.stats() for mesh in meshes]
     secs = sum(times)
     t_all, units_all = aggregate(dist, secs, units, "cuda")
@@ -641,19 +643,22 @@ def run_batch(args):
         "dtype": "f32", "data": "synthetic", "config": config,
         "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99)),
                        "what": "one batch of 64 jobs, seeds to 1000 steps"},
-        "vs_plain": {"value": units_plain / t_plain, "unit": UNIT, "speedup": (units / secs) / (units_plain / t_plain),
-                     "desc": "the same jobs stepped one after another with lf_step on this GPU"},
+        "vs_plain": None if t_plain is None else
+        {"value": units_plain / t_plain, "unit": UNIT, "speedup": (units / secs) / (units_plain / t_plain),
+         "desc": "the same jobs stepped one after another with lf_step on this GPU"},
         "schedules": {("tuned" if args.schedule == "auto" else args.schedule): units / secs,
                       **{f"all_{k}": v for k, v in fixed.items()}, "unit": UNIT,
                       "jobs": {k: tuned.count(v) for k, v in lf.SCHEDULES.items()}, "tune_s": t_tune,
                       "desc": f"per job, lf_tune after {TUNE_AT} steps ({TUNE_TRIAL} steps per schedule and round, "
-                              "two rounds) picks the step kernel's register allocation for 4, 5 or 3 CTAs per SM "
-                              "(same bits); the batch under the tuned schedules against every job under one "
-                              "fixed schedule"},
+                              "two rounds) picks the step kernel's register allocation for 4, 5 or 3 CTAs per SM, "
+                              "the lean register-tier path with the full step for the tiles outside it, or the lean gather with "
+                              "the other tiers per vertex (same bits); the "
+                              "batch under the tuned schedules against every job under one fixed schedule"},
         "roofline": roofline,
-        "e2e": {"value": e2e_units / t_e2e, "unit": UNIT,
-                "h2d_bytes_per_step": int(sum(24 * m.n_v + 12 * m.n_f + 4 * len(sd) for m, sd in zip(geo, seeds))),
-                "d2h_bytes_per_step": int(4 * n_v_total), "jobs": len(specs)},
+        "e2e": None if t_e2e is None else
+        {"value": e2e_units / t_e2e, "unit": UNIT,
+         "h2d_bytes_per_step": int(sum(24 * m.n_v + 12 * m.n_f + 4 * len(sd) for m, sd in zip(geo, seeds))),
+         "d2h_bytes_per_step": int(4 * n_v_total), "jobs": len(specs)},
         "gpu_launches": launches * roofline["launches_per_step"] + retries,
         "clocks": clk_summary,
     }
@@ -926,7 +931,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--order", choices=["generated", "locality"], default="generated",
                     help="batch64: the meshes' vertex numbering (locality: renumbered before lf_create_mesh)")
-    ap.add_argument("--schedule", choices=["auto", "ctas4", "ctas5", "ctas3"], default="auto",
+    ap.add_argument("--timed-only", action="store_true",
+                    help="batch64: time the batch only, without the fixed-schedule, one-at-a-time and end-to-end "
+                         "runs (the command the profiles capture)")
+    ap.add_argument("--schedule", choices=["auto", "ctas4", "ctas5", "ctas3", "hot", "lean"], default="auto",
                     help="batch64: the step-kernel schedule of every job (auto: lf_tune per job)")
     args = ap.parse_args()
     batch = args.workload == "batch64"

@@ -329,13 +329,24 @@ lf_status lf_step_noalloc(void* cuda_stream, int32_t n_v, int32_t n_layers,
 
 /*
  * Step-kernel schedules (no counterpart in the paper, which runs one mesh).
- * The step kernel is compiled three times, its registers allocated for 4
- * (schedule 0, the default), 5 (schedule 1) and 3 (schedule 2) resident CTAs
- * per SM (the FP32 kernel takes 62, 48 and 79 registers a thread).  All give the same bits; which is
- * fastest depends on the job: more resident warps hide the gather's latency
- * on large meshes, more registers per thread help small ones (measured on
- * GB300 in steady state: a 1024^2 torus 83.1 / 84.4 / 93.4 us a step under
- * schedules 1 / 0 / 2, a 150^2 torus 20.4 / 19.3 / 18.2 us).  Jobs with
+ * Schedules 0, 1 and 2 are the step kernel with its registers allocated for
+ * 4 (the default), 5 and 3 resident CTAs per SM (the FP32 kernel takes 64,
+ * 48 and 80 registers a thread).  Schedule 3 runs a lean register-tier path
+ * (every vertex of a tile holding at most five cells and the base layer and
+ * seeing at most five cells in its closed neighbourhood; four neighbours'
+ * loads in flight a thread, branch-free slot updates) and the full step on
+ * any other tile, in the same launch.  Schedule 4 is the step kernel with
+ * that lean gather as its register tier and, per vertex, the shared-memory
+ * and storage-free tiers beyond it.  All give the same bits.  Which is
+ * fastest depends on the job and on its state: more resident warps hide the
+ * gather's latency on large meshes, more registers per thread help small
+ * ones, schedule 3 pays once the cells have formed but does a tile twice
+ * while a vertex of it is outside its shape (fronts meeting, crowded
+ * junctions), and schedule 4 sits between.  Measured on GB300 in steady
+ * state (us a step under schedules 0 / 3 / 4): a 1024^2 torus with 8192
+ * cells 84.5 / 76.3 / 81.7, a 150^2 torus with 500 cells 19.6 / 10.0 / 10.2,
+ * a level-7 icosphere with 2000 cells 18.3 / 15.3 / 15.8, and a level-8
+ * icosphere with 300 cells, its fronts still meeting, 32.6 / 36.5 / 37.6.  Jobs with
  * coefficient matrices always take the general-coefficient kernel at 4 CTAs.
  * lf_set_schedule fixes a job's schedule; lf_schedule reads it (-1 for
  * NULL).  lf_tune is the autotuner: it runs trial_steps time-iterations under

@@ -262,7 +262,10 @@ def lf_step(mesh, n_iters):
     _check(_lib.lf_step(mesh, int(n_iters)), mesh)
 
 
-SCHEDULES = {"ctas4": 0, "ctas5": 1, "ctas3": 2}    # the step kernel's resident CTAs per SM
+# the step kernel's resident CTAs per SM; the lean register-tier path with the
+# full step for the tiles outside its shape; the lean gather with the other
+# tiers per vertex
+SCHEDULES = {"ctas4": 0, "ctas5": 1, "ctas3": 2, "hot": 3, "lean": 4}
 
 
 def lf_set_schedule(mesh, schedule):
@@ -411,7 +414,7 @@ class Mesh:
         lf_step(self.h, n)
 
     def set_schedule(self, schedule):
-        """0 / "ctas4" (the default), 1 / "ctas5" or 2 / "ctas3": the same bits either way."""
+        """0 / "ctas4" (the default), 1 / "ctas5", 2 / "ctas3", 3 / "hot" or 4 / "lean": the same bits."""
         lf_set_schedule(self.h, schedule)
 
     @property

@@ -111,13 +111,21 @@ int step_slots();
 // the form for general coefficient matrices or not; its only argument is a
 // BatchParams.
 // Step-kernel schedules: the register allocation of the step kernel for 4,
-// 5 or 3 resident CTAs per SM (62, 48 and 79 registers a thread in FP32).  All give
+// 5 or 3 resident CTAs per SM (64, 48 and 80 registers a thread in FP32).  All give
 // the same bits; which is fastest depends on the job (its size against the
 // GPU, its degree and its cells).
 constexpr int kSched4 = 0;      // the default
 constexpr int kSched5 = 1;
 constexpr int kSched3 = 2;
-constexpr int kSchedules = 3;
+// The register-tier kernel: a tile whose every vertex holds at most five
+// cells and the base layer and sees at most five cells in its closed
+// neighbourhood takes a lean path; any other tile takes the full step in the
+// same launch.
+constexpr int kSchedHot = 3;
+// The step kernel with the lean path's gather in its fast tier and, per
+// vertex, the other tiers beyond it (at 4 CTAs per SM).
+constexpr int kSchedLean = 4;
+constexpr int kSchedules = 5;
 // A launch kind: the storage type and the schedule of the jobs in one launch.
 inline int step_kind(int dtype, int sched) { return dtype + 3 * sched; }
 const void* step_kernel(int kind, bool general);

@@ -89,7 +89,15 @@ constexpr int kBlock = kTile;   // threads (= vertices) per CTA
 #define LF_SLOTS 5
 #endif
 constexpr int kSlots = LF_SLOTS; // register map slots of the fast path
-constexpr int kChunk = 2;       // neighbours fetched per batch
+constexpr int kChunk = 2;       // neighbours fetched per batch (register-map tier)
+#ifndef LF_CHUNK0
+#define LF_CHUNK0 4
+#endif
+constexpr int kChunk0 = LF_CHUNK0;  // neighbours fetched per batch (lean gather)
+#ifndef LF_HOT_CELLS
+#define LF_HOT_CELLS 5
+#endif
+constexpr int kHotCells = LF_HOT_CELLS;   // cells in the lean gather's register map
 constexpr int kPool = 4;        // medium-path maps per CTA
 constexpr int kMed = 32;        // slots of a medium-path map
 
@@ -312,29 +320,30 @@ __device__ float slow_general_value(const Neighbourhood<DT>& nb, const GenCoef& 
   return gc.value(Fj, root(Fj), Aj, Wj, Ej, sumA, sumW, fn);
 }
 
-// Register map of the fast path: layer id (-1 = empty), G and F per slot.
-struct SlotMap {
-  int id[kSlots];
-  float g[kSlots];
-  float f[kSlots];
+// Register map of K slots: layer id (-1 = empty), G and F per slot.
+template <int K>
+struct SlotMapT {
+  int id[K];
+  float g[K];
+  float f[K];
   int cnt;
 
   __device__ __forceinline__ void clear() {
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) { id[s] = -1; g[s] = 0.0f; f[s] = 0.0f; }
+    for (int s = 0; s < K; ++s) { id[s] = -1; g[s] = 0.0f; f[s] = 0.0f; }
     cnt = 0;
   }
   // Adds x to the slot of layer l, opening a slot if needed.  False when full.
   __device__ __forceinline__ bool add(int l, float x) {
     bool found = false;
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
+    for (int s = 0; s < K; ++s) {
       if (s < cnt && !found && id[s] == l) { g[s] = __fadd_rn(g[s], x); found = true; }
     }
     if (found) return true;
-    if (cnt >= kSlots - 1) return false;    // one slot stays for the base layer
+    if (cnt >= K - 1) return false;    // one slot stays for the base layer
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
+    for (int s = 0; s < K; ++s) {
       if (s == cnt) { id[s] = l; g[s] = x; }
     }
     ++cnt;
@@ -348,46 +357,43 @@ struct SlotMap {
     g[a] = sw ? gb : ga;  g[b] = sw ? ga : gb;
     f[a] = sw ? fb : fa;  f[b] = sw ? fa : fb;
   }
-  // The first M slots in ascending id order (empty slots, -1, last): the
-  // warp's lanes use at most M slots, so the rest are empty everywhere.
+  // The first M slots in ascending id order (ids are distinct; empty slots,
+  // -1, sort last).  A warp's lanes use at most M + 1 slots and the base
+  // layer, the largest id, is each lane's last live slot, so ordering the
+  // first min(M, K - 1) slots orders every live one: optimal networks for
+  // two to five slots (one, three, five and nine exchanges), odd-even
+  // transposition beyond.
   template <int M>
   __device__ __forceinline__ void sort_first() {
     if constexpr (M == 2) {
       cswap(0, 1);
     } else if constexpr (M == 3) {
       cswap(0, 1); cswap(1, 2); cswap(0, 1);
-    } else if constexpr (M >= 4) {
-      sort();
-    }
-  }
-  // Sorting network on the cell slots (ids are distinct; empty slots hold -1,
-  // which sorts last).  The base layer, the largest id, is the last live
-  // slot, so ordering the first kSlots - 1 slots orders them all: the optimal
-  // five exchanges for four, odd-even transposition otherwise.
-  __device__ __forceinline__ void sort() {
-    if constexpr (kSlots - 1 == 4) {
+    } else if constexpr (M == 4) {
       cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
-    } else {
+    } else if constexpr (M == 5) {
+      cswap(0, 1); cswap(3, 4); cswap(2, 4); cswap(2, 3); cswap(1, 4);
+      cswap(0, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
+    } else if constexpr (M > 5) {
 #pragma unroll
-      for (int r = 0; r < kSlots - 1; ++r)
+      for (int r = 0; r < M; ++r)
 #pragma unroll
-        for (int a = r & 1; a + 1 < kSlots - 1; a += 2) cswap(a, a + 1);
+        for (int a = r & 1; a + 1 < M; a += 2) cswap(a, a + 1);
     }
   }
 };
+using SlotMap = SlotMapT<kSlots>;
 
 // Runs fn with the number of register slots a warp's lanes use at most as a
-// compile-time constant, so that the per-slot loops after the gather unroll
-// over the live slots only (n is warp-uniform).
-static_assert(kSlots == 5, "with_slots spells out the slot counts 1 to 5");
-template <class Fn>
+// compile-time constant (1 to K), so that the per-slot loops after the gather
+// unroll over the live slots only (n is warp-uniform).
+template <int K, int M = 1, class Fn>
 __device__ __forceinline__ void with_slots(int n, Fn&& fn) {
-  switch (n) {
-    case 1: fn(std::integral_constant<int, 1>{}); break;
-    case 2: fn(std::integral_constant<int, 2>{}); break;
-    case 3: fn(std::integral_constant<int, 3>{}); break;
-    case 4: fn(std::integral_constant<int, 4>{}); break;
-    default: fn(std::integral_constant<int, 5>{}); break;
+  if constexpr (M >= K) {
+    fn(std::integral_constant<int, K>{});
+  } else {
+    if (n <= M) fn(std::integral_constant<int, M>{});
+    else with_slots<K, M + 1>(n, fn);
   }
 }
 
@@ -415,10 +421,10 @@ struct MedMap {
 // order, the skeleton test, the per-vertex sums, Algorithm 1's update (the
 // class closed form or the general matrices), the clamp, the normalisation
 // and the rounding to the storage type.
-template <int DT, bool GEN, int N>
-__device__ __forceinline__ void slot_update(SlotMap& mp, const int own_cells, const int own, const float dsum,
+template <int DT, bool GEN, int N, int K>
+__device__ __forceinline__ void slot_update(SlotMapT<K>& mp, const int own_cells, const int own, const float dsum,
                                             const int base, const Coefs& c, const GenCoef& gc, const bool general,
-                                            VertexSums& S, float (&vnew)[kSlots], bool (&keep)[kSlots], int& kept,
+                                            VertexSums& S, float (&vnew)[K], bool (&keep)[K], int& kept,
                                             float& tot, bool& zero_sum) {
   using V = Val<DT>;
     // diagonal: the own entries (the own cells, then the base layer)
@@ -428,7 +434,7 @@ __device__ __forceinline__ void slot_update(SlotMap& mp, const int own_cells, co
     // slots in ascending layer order (empty slots, id -1, last): the sums
     // below then run in the same order as on the other paths, and the row
     // is written in slot order
-    mp.template sort_first<(N < kSlots - 1 ? N : kSlots - 1)>();
+    mp.template sort_first<(N < K - 1 ? N : K - 1)>();
     float sq[N];
 #pragma unroll
     for (int s = 0; s < N; ++s) sq[s] = root(mp.f[s]);
@@ -487,8 +493,8 @@ __device__ __forceinline__ void slot_update(SlotMap& mp, const int own_cells, co
 }
 
 // Writes the kept entries of a register map of N slots in slot order.
-template <int DT, int N, class Put>
-__device__ __forceinline__ void slot_write(const SlotMap& mp, const bool (&keep)[kSlots], const float (&vnew)[kSlots],
+template <int DT, int N, int K, class Put>
+__device__ __forceinline__ void slot_write(const SlotMapT<K>& mp, const bool (&keep)[K], const float (&vnew)[K],
                                            int off, Put& put) {
   using V = Val<DT>;
   int o = off;
@@ -500,17 +506,98 @@ __device__ __forceinline__ void slot_write(const SlotMap& mp, const bool (&keep)
   }
 }
 
+// G = sum_j L_ij F(j, .) over the register map, lean form: the neighbours in
+// batches of kChunk0 (their L entries, then their head records, loaded before
+// any is used), every entry through one compare over the cell slots, a cell
+// new to the map opening the first empty slot (the map's cells fill its
+// first slots, the rest hold -1), the base layer summed apart in gB.
+// Each layer's sum runs in the row order of L, as on every other path.  The
+// sum of the row's off-diagonal weights goes to nb.dsum.  False when a cell
+// found no free slot (one stays for the base layer); the map is then
+// incomplete and only nb.dsum is final.  mp.cnt: the cells in the map.
+template <int DT, int K>
+__device__ __forceinline__ bool lean_gather(Neighbourhood<DT>& nb, const int4* __restrict__ head, const int base,
+                                            SlotMapT<K>& mp, float& gB) {
+  using V = Val<DT>;
+  bool fit = true;
+  // slots fill in order (empty ones hold -1): a cell new to the map opens the
+  // first empty slot; every update is a select, no branch
+  auto add = [&](int l, float x, bool live) {
+    const bool isb = live && l == base;
+    gB = isb ? __fadd_rn(gB, x) : gB;
+    const int cell = (live && !isb) ? l : -2;
+    bool m[K - 1];
+    bool fresh = cell >= 0;
+#pragma unroll
+    for (int s2 = 0; s2 < K - 1; ++s2) {
+      m[s2] = cell == mp.id[s2];
+      fresh = fresh && !m[s2];
+    }
+    fit = fit && !(fresh && mp.id[K - 2] >= 0);
+    bool o[K - 1];
+#pragma unroll
+    for (int s2 = 0; s2 < K - 1; ++s2) o[s2] = fresh && mp.id[s2] < 0 && (s2 == 0 || mp.id[s2 - 1] >= 0);
+#pragma unroll
+    for (int s2 = 0; s2 < K - 1; ++s2) {
+      mp.g[s2] = o[s2] ? x : (m[s2] ? __fadd_rn(mp.g[s2], x) : mp.g[s2]);
+      mp.id[s2] = o[s2] ? cell : mp.id[s2];
+    }
+  };
+  for (int qb = nb.q0; qb < nb.q1; qb += kChunk0) {
+    int2 cv[kChunk0];
+#pragma unroll
+    for (int k = 0; k < kChunk0; ++k) {
+      cv[k] = make_int2(-1, 0);
+      if (qb + k < nb.q1) cv[k] = __ldg(nb.Lcv + LF_CK(nb, qb + k, nb.L_nnz));
+    }
+    int4 hj[kChunk0];
+#pragma unroll
+    for (int k = 0; k < kChunk0; ++k) {
+      hj[k] = make_int4(0, 0, 0, 0);
+      if (cv[k].x >= 0) hj[k] = __ldg(head + LF_CK(nb, cv[k].x, nb.n_v));
+    }
+#pragma unroll
+    for (int k = 0; k < kChunk0; ++k) {
+      if (cv[k].x < 0) continue;
+      const float lij = __int_as_float(cv[k].y);
+      nb.dsum += lij;
+      if (!fit) continue;
+      const int rn = hj[k].x;
+      const int e1 = (hj[k].y >> 16) & 0xffff;
+      add(hj[k].y & 0xffff, __fmul_rn(lij, V::from_bits(hj[k].z)), rn >= 1);
+      if (rn >= 2) {
+        const float x1 = __fmul_rn(lij, V::from_bits(hj[k].w));
+        if (e1 == base) gB = __fadd_rn(gB, x1);
+        else add(e1, x1, true);                // a row of two cells
+      }
+      if (rn > 2) {                              // rows of three entries or more
+        const int rs = __ldg(nb.rows + LF_CK(nb, cv[k].x, nb.n_v)).x;
+        for (int p = 2; p < rn; ++p)
+          add(__ldg(nb.Fid + LF_CK(nb, rs + p, nb.entries)),
+              __fmul_rn(lij, V::load(nb.Fval + LF_CK(nb, rs + p, nb.entries))), true);
+      }
+    }
+  }
+  int n = 0;
+#pragma unroll
+  for (int s2 = 0; s2 < K - 1; ++s2) n += mp.id[s2] >= 0;
+  mp.cnt = n;
+  return fit;
+}
+
 // ---------------------------------------------------------------------------
 // the step kernel
 // ---------------------------------------------------------------------------
 enum : int { kFast = 0, kMedium = 1, kSlow = 2 };
 
-// MINB: CTAs per SM the register allocation is made for (the schedule).
-template <int DT, bool GEN, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_constant__ BatchParams P) {
+// One step of the tile of this CTA with every tier: the body of the step
+// kernel, and of the register-tier kernel for a tile outside its shape.
+template <int DT, bool GEN, bool LEAN>
+__device__ __forceinline__ void step_tile(const BatchParams& P) {
   using V = Val<DT>;
   using T = typename V::T;
   constexpr int kWarps = kBlock / 32;
+  constexpr int K = LEAN ? kHotCells + 1 : kSlots;   // register-map slots
   __shared__ uint32_t s_err;
   __shared__ int s_pool;
   __shared__ unsigned s_red[kWarps];
@@ -518,9 +605,6 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
   __shared__ int s_med_id[kPool][kMed];
   __shared__ float s_med_g[kPool][kMed];
   __shared__ float s_med_f[kPool][kMed];
-
-  wait_previous_grid();
-  allow_next_grid();
 
   // ---- the job of this CTA (uniform): last j with tile_start[j] <= blockIdx.x
   int lo = 0, hi = P.n_jobs - 1;
@@ -596,16 +680,16 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
   __syncthreads();
   if (s_err) return;                 // an earlier step of this job failed
 
-  SlotMap mp;
+  SlotMapT<K> mp;
   mp.clear();
   int mode = kFast;
   bool zero_sum = false;
   int kept = 0, nsk = 0;
   const int own = h_own.x;
-  float vnew[kSlots];
-  bool keep[kSlots];
+  float vnew[K];
+  bool keep[K];
 #pragma unroll
-  for (int s = 0; s < kSlots; ++s) { vnew[s] = 0.0f; keep[s] = false; }
+  for (int s = 0; s < K; ++s) { vnew[s] = 0.0f; keep[s] = false; }
   VertexSums S = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, 0};
   float tot = 0.0f;
   MedMap med;
@@ -619,7 +703,7 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
   float gB = 0.0f, fB = 0.0f;
   int own_cells = own;              // own entries other than the base layer
   if (i < n_v) {
-    if (own > kSlots) {
+    if (own > K) {
       mode = kMedium;
     } else if (own <= 2) {
       if (own > 0) {
@@ -633,7 +717,7 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
     } else {
       read_own_row();
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
+      for (int s = 0; s < K; ++s) {
         if (s < own) {
           mp.id[s] = __ldg(nb.Fid + LF_CK(nb, nb.p0 + s, nb.entries));
           mp.f[s] = V::load(nb.Fval + LF_CK(nb, nb.p0 + s, nb.entries));
@@ -646,7 +730,7 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
       int last = -1;
       float flast = 0.0f;
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
+      for (int s = 0; s < K; ++s) {
         last = (s == own - 1) ? mp.id[s] : last;
         flast = (s == own - 1) ? mp.f[s] : flast;
       }
@@ -654,125 +738,131 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
         fB = flast;
         own_cells = own - 1;
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s)
+        for (int s = 0; s < K; ++s)
           if (s == own - 1) { mp.id[s] = -1; mp.f[s] = 0.0f; }
       }
     }
     mp.cnt = own_cells;
-    // ---- G = sum_j L_ij F(j, .): neighbours in batches of kChunk; the head
-    // records of the batch's rows are loaded before any is used
-    for (int qb = nb.q0; qb < nb.q1; qb += kChunk) {
-      int jj[kChunk], rn[kChunk];
-      float lij[kChunk];
-#pragma unroll
-      for (int k = 0; k < kChunk; ++k) {
-        jj[k] = -1;
-        lij[k] = 0.0f;
-        if (qb + k < nb.q1) {
-          const int2 cv = __ldg(nb.Lcv + LF_CK(nb, qb + k, nb.L_nnz));
-          jj[k] = cv.x;
-          lij[k] = __int_as_float(cv.y);
-        }
-      }
-      int4 hj[kChunk];
-#pragma unroll
-      for (int k = 0; k < kChunk; ++k) {
-        hj[k] = make_int4(0, 0, 0, 0);
-        if (jj[k] >= 0) {
-          hj[k] = __ldg(in.head + LF_CK(nb, jj[k], nb.n_v));
-          nb.dsum += lij[k];
-        }
-        rn[k] = hj[k].x;
-      }
-      if (mode != kFast) continue;
-      // the first two entries of each row of the batch; -2 marks "no entry"
-      int e0[kChunk], e1[kChunk];
-      float x0[kChunk], x1[kChunk];
-      bool simple = true;           // every row: at most a cell, then the base layer
-#pragma unroll
-      for (int k = 0; k < kChunk; ++k) {
-        e0[k] = e1[k] = -2;
-        x0[k] = x1[k] = 0.0f;
-        if (rn[k] > 0) {
-          e0[k] = hj[k].y & 0xffff;
-          x0[k] = __fmul_rn(lij[k], V::from_bits(hj[k].z));
-        }
-        if (rn[k] > 1) {
-          e1[k] = (hj[k].y >> 16) & 0xffff;
-          x1[k] = __fmul_rn(lij[k], V::from_bits(hj[k].w));
-        }
-        simple = simple && rn[k] <= 2 && (rn[k] < 2 || e1[k] == base);
-      }
-      if (simple) {
-        // base contributions, one per row at most, in row order
+    if constexpr (LEAN) {
+      // ---- G = sum_j L_ij F(j, .), lean form; a vertex whose cells outgrow
+      // the map takes the medium path (the weights' sum is complete either way)
+      if (!lean_gather(nb, in.head, base, mp, gB)) mode = kMedium;
+    } else {
+      // ---- G = sum_j L_ij F(j, .): neighbours in batches of kChunk; the head
+      // records of the batch's rows are loaded before any is used
+      for (int qb = nb.q0; qb < nb.q1; qb += kChunk) {
+        int jj[kChunk], rn[kChunk];
+        float lij[kChunk];
 #pragma unroll
         for (int k = 0; k < kChunk; ++k) {
-          gB = (e0[k] == base) ? __fadd_rn(gB, x0[k]) : gB;
-          gB = (e1[k] == base) ? __fadd_rn(gB, x1[k]) : gB;
-          if (e0[k] == base) e0[k] = -2;
-        }
-        // cell entries (first entries only): slot x entry compare matrix, each
-        // slot summing its entries in row order (empty slots hold -1)
-        bool hit[kChunk];
-#pragma unroll
-        for (int k = 0; k < kChunk; ++k) hit[k] = e0[k] < 0;
-        // over the cell slots that the lanes here have opened at most (the
-        // slots beyond are empty in every lane)
-        auto matrix = [&](auto cells) {
-#pragma unroll
-          for (int s2 = 0; s2 < decltype(cells)::value; ++s2) {
-#pragma unroll
-            for (int k = 0; k < kChunk; ++k) {
-              const bool m = e0[k] == mp.id[s2];
-              mp.g[s2] = m ? __fadd_rn(mp.g[s2], x0[k]) : mp.g[s2];
-              hit[k] = hit[k] || m;
-            }
-          }
-        };
-        const int open_cells = __reduce_max_sync(__activemask(), mp.cnt);
-        if (open_cells <= 1) matrix(std::integral_constant<int, 1>{});
-        else if (open_cells == 2) matrix(std::integral_constant<int, 2>{});
-        else matrix(std::integral_constant<int, kSlots - 1>{});
-        // cells new to the map, in row order: a missed entry opens the next
-        // slot (no existing slot can match it: the matrix above compared them
-        // all); when both entries of the batch miss with the same layer, one
-        // slot opens with their sum taken in row order
-        static_assert(kChunk == 2, "the miss handling below is written for batches of two");
-        const bool m0 = !hit[0], m1 = !hit[1];
-        if (m0 || m1) {
-          const bool same = m0 && m1 && e0[0] == e0[1];
-          const int la = m0 ? e0[0] : e0[1];
-          const float xa = m0 ? (same ? __fadd_rn(x0[0], x0[1]) : x0[0]) : x0[1];
-          const bool second = m0 && m1 && !same;
-          if (mp.cnt + (second ? 1 : 0) >= kSlots - 1) {
-            mode = kMedium;                    // one slot stays for the base layer
-          } else {
-#pragma unroll
-            for (int s2 = 0; s2 < kSlots - 1; ++s2) {
-              if (s2 == mp.cnt) { mp.id[s2] = la; mp.g[s2] = xa; }
-              if (second && s2 == mp.cnt + 1) { mp.id[s2] = e0[1]; mp.g[s2] = x0[1]; }
-            }
-            mp.cnt += second ? 2 : 1;
+          jj[k] = -1;
+          lij[k] = 0.0f;
+          if (qb + k < nb.q1) {
+            const int2 cv = __ldg(nb.Lcv + LF_CK(nb, qb + k, nb.L_nnz));
+            jj[k] = cv.x;
+            lij[k] = __int_as_float(cv.y);
           }
         }
-      } else {
-        // rows with two cells or more than two entries (transients, band
-        // vertices): every entry in row order, strictly sequential
+        int4 hj[kChunk];
 #pragma unroll
         for (int k = 0; k < kChunk; ++k) {
-          if (rn[k] <= 0 || mode != kFast) continue;
-          const int start = rn[k] > 2 ? __ldg(nb.rows + LF_CK(nb, jj[k], nb.n_v)).x : 0;
-          for (int p = 0; p < rn[k] && mode == kFast; ++p) {
-            int l;
-            float x;
-            if (p == 0) { l = e0[k]; x = x0[k]; }
-            else if (p == 1) { l = e1[k]; x = x1[k]; }
-            else {
-              l = __ldg(nb.Fid + LF_CK(nb, start + p, nb.entries));
-              x = __fmul_rn(lij[k], V::load(nb.Fval + LF_CK(nb, start + p, nb.entries)));
+          hj[k] = make_int4(0, 0, 0, 0);
+          if (jj[k] >= 0) {
+            hj[k] = __ldg(in.head + LF_CK(nb, jj[k], nb.n_v));
+            nb.dsum += lij[k];
+          }
+          rn[k] = hj[k].x;
+        }
+        if (mode != kFast) continue;
+        // the first two entries of each row of the batch; -2 marks "no entry"
+        int e0[kChunk], e1[kChunk];
+        float x0[kChunk], x1[kChunk];
+        bool simple = true;           // every row: at most a cell, then the base layer
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+          e0[k] = e1[k] = -2;
+          x0[k] = x1[k] = 0.0f;
+          if (rn[k] > 0) {
+            e0[k] = hj[k].y & 0xffff;
+            x0[k] = __fmul_rn(lij[k], V::from_bits(hj[k].z));
+          }
+          if (rn[k] > 1) {
+            e1[k] = (hj[k].y >> 16) & 0xffff;
+            x1[k] = __fmul_rn(lij[k], V::from_bits(hj[k].w));
+          }
+          simple = simple && rn[k] <= 2 && (rn[k] < 2 || e1[k] == base);
+        }
+        if (simple) {
+          // base contributions, one per row at most, in row order
+#pragma unroll
+          for (int k = 0; k < kChunk; ++k) {
+            gB = (e0[k] == base) ? __fadd_rn(gB, x0[k]) : gB;
+            gB = (e1[k] == base) ? __fadd_rn(gB, x1[k]) : gB;
+            if (e0[k] == base) e0[k] = -2;
+          }
+          // cell entries (first entries only): slot x entry compare matrix, each
+          // slot summing its entries in row order (empty slots hold -1)
+          bool hit[kChunk];
+#pragma unroll
+          for (int k = 0; k < kChunk; ++k) hit[k] = e0[k] < 0;
+          // over the cell slots that the lanes here have opened at most (the
+          // slots beyond are empty in every lane)
+          auto matrix = [&](auto cells) {
+#pragma unroll
+            for (int s2 = 0; s2 < decltype(cells)::value; ++s2) {
+#pragma unroll
+              for (int k = 0; k < kChunk; ++k) {
+                const bool m = e0[k] == mp.id[s2];
+                mp.g[s2] = m ? __fadd_rn(mp.g[s2], x0[k]) : mp.g[s2];
+                hit[k] = hit[k] || m;
+              }
             }
-            if (l == base) gB = __fadd_rn(gB, x);
-            else if (!mp.add(l, x)) mode = kMedium;
+          };
+          const int open_cells = __reduce_max_sync(__activemask(), mp.cnt);
+          if (open_cells <= 1) matrix(std::integral_constant<int, 1>{});
+          else if (open_cells == 2) matrix(std::integral_constant<int, 2>{});
+          else matrix(std::integral_constant<int, K - 1>{});
+          // cells new to the map, in row order: a missed entry opens the next
+          // slot (no existing slot can match it: the matrix above compared them
+          // all); when both entries of the batch miss with the same layer, one
+          // slot opens with their sum taken in row order
+          static_assert(kChunk == 2, "the miss handling below is written for batches of two");
+          const bool m0 = !hit[0], m1 = !hit[1];
+          if (m0 || m1) {
+            const bool same = m0 && m1 && e0[0] == e0[1];
+            const int la = m0 ? e0[0] : e0[1];
+            const float xa = m0 ? (same ? __fadd_rn(x0[0], x0[1]) : x0[0]) : x0[1];
+            const bool second = m0 && m1 && !same;
+            if (mp.cnt + (second ? 1 : 0) >= K - 1) {
+              mode = kMedium;                    // one slot stays for the base layer
+            } else {
+#pragma unroll
+              for (int s2 = 0; s2 < K - 1; ++s2) {
+                if (s2 == mp.cnt) { mp.id[s2] = la; mp.g[s2] = xa; }
+                if (second && s2 == mp.cnt + 1) { mp.id[s2] = e0[1]; mp.g[s2] = x0[1]; }
+              }
+              mp.cnt += second ? 2 : 1;
+            }
+          }
+        } else {
+          // rows with two cells or more than two entries (transients, band
+          // vertices): every entry in row order, strictly sequential
+#pragma unroll
+          for (int k = 0; k < kChunk; ++k) {
+            if (rn[k] <= 0 || mode != kFast) continue;
+            const int start = rn[k] > 2 ? __ldg(nb.rows + LF_CK(nb, jj[k], nb.n_v)).x : 0;
+            for (int p = 0; p < rn[k] && mode == kFast; ++p) {
+              int l;
+              float x;
+              if (p == 0) { l = e0[k]; x = x0[k]; }
+              else if (p == 1) { l = e1[k]; x = x1[k]; }
+              else {
+                l = __ldg(nb.Fid + LF_CK(nb, start + p, nb.entries));
+                x = __fmul_rn(lij[k], V::load(nb.Fval + LF_CK(nb, start + p, nb.entries)));
+              }
+              if (l == base) gB = __fadd_rn(gB, x);
+              else if (!mp.add(l, x)) mode = kMedium;
+            }
           }
         }
       }
@@ -780,11 +870,11 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
     // the base layer joins the slots last (largest id); with six cells
     // already there the vertex takes the next tier
     if (mode == kFast) {
-      if (mp.cnt >= kSlots) {
+      if (mp.cnt >= K) {
         mode = kMedium;
       } else {
 #pragma unroll
-        for (int s2 = 0; s2 < kSlots; ++s2) {
+        for (int s2 = 0; s2 < K; ++s2) {
           if (s2 == mp.cnt) { mp.id[s2] = base; mp.g[s2] = gB; mp.f[s2] = fB; }
         }
         ++mp.cnt;
@@ -840,7 +930,7 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
       // over the slots that the lanes here use at most (every lane's own
       // count is within it, whichever lanes run this together)
       // (the general form keeps all slots: its matrix sums are the cost there)
-      with_slots(GEN ? kSlots : __reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
+      with_slots<K>(GEN ? K : __reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
         slot_update<DT, GEN, decltype(slots)::value>(mp, own_cells, own, nb.dsum, base, c, gc, general, S, vnew, keep,
                                                      kept, tot, zero_sum);
       });
@@ -988,8 +1078,8 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
     if (mode == kFast) {
       int top = 1;                             // slots up to the last kept one
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) top = keep[s] ? s + 1 : top;
-      with_slots(GEN ? kSlots : __reduce_max_sync(__activemask(), top), [&](auto slots) {
+      for (int s = 0; s < K; ++s) top = keep[s] ? s + 1 : top;
+      with_slots<K>(GEN ? K : __reduce_max_sync(__activemask(), top), [&](auto slots) {
         slot_write<DT, decltype(slots)::value>(mp, keep, vnew, off, put);
       });
     } else if (mode == kMedium) {
@@ -1015,6 +1105,232 @@ __global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_co
         }
       }
     }
+    out.head[i] = ho;
+  }
+
+  // ---- end of step: the last CTA of the job commits the step ----------------
+  if (t == 0) {
+    atomicAdd(&st->skeleton_step, static_cast<unsigned long long>(tile_sk));
+    atomicAdd(&st->nnz_step, static_cast<unsigned long long>(tile_total));
+    __threadfence();
+    const uint32_t prev = atomicAdd(&st->done, 1u);
+    if (prev == static_cast<uint32_t>(J.num_tiles) - 1u) {
+      __threadfence();
+      if (ld_relaxed_u32(&st->err) == 0u) {
+        const unsigned long long nin = ld_relaxed(&st->nnz);
+        const unsigned long long nout = ld_relaxed(&st->nnz_step);
+        st->skeleton_total = ld_relaxed(&st->skeleton_total) + ld_relaxed(&st->skeleton_step);
+        st->nnz_io_total = ld_relaxed(&st->nnz_io_total) + nin + nout;
+        st->nnz = nout;
+        st->epoch = st->epoch + 1u;
+      }
+      st->skeleton_step = 0ull;
+      st->nnz_step = 0ull;
+      st->done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// MINB: CTAs per SM the register allocation is made for (the schedule).
+// LEAN: the fast tier's gather in its lean form (schedule kSchedLean).
+template <int DT, bool GEN, int MINB, bool LEAN = false>
+__global__ void __launch_bounds__(kBlock, MINB) step_kernel_impl(const __grid_constant__ BatchParams P) {
+  wait_previous_grid();
+  allow_next_grid();
+  step_tile<DT, GEN, LEAN>(P);
+}
+
+// ---------------------------------------------------------------------------
+// the register-tier kernel (schedule kSchedHot)
+// ---------------------------------------------------------------------------
+// The same time-iteration as step_kernel_impl for the tiles whose every vertex
+// holds at most kHotCells cells and the base layer itself and sees at most
+// kHotCells cells in its closed neighbourhood: the register-map tier alone.  A cell's
+// sum opens on the first entry of that cell and every later entry of it adds
+// to it, in the order of the row of L, so every layer's sum -- and so the
+// result -- is that of the other tiers, bit for bit.  A tile with a vertex
+// outside the shape writes nothing here and takes the full step (every tier)
+// instead, in the same CTA.  The lean path has fewer instructions a vertex
+// and more neighbours' loads in flight; it pays wherever the shape holds on
+// nearly every tile, which is the steady state once the cells have formed.
+template <int DT>
+__global__ void __launch_bounds__(kBlock, 4) step_kernel_hot(const __grid_constant__ BatchParams P) {
+  using V = Val<DT>;
+  using T = typename V::T;
+  constexpr int kWarps = kBlock / 32;
+  constexpr int K = kHotCells + 1;                // slots: the cells', then the base layer's
+  __shared__ uint32_t s_err;
+  __shared__ unsigned s_red[kWarps];
+  __shared__ int s_warp_cnt[kWarps];
+
+  wait_previous_grid();
+  allow_next_grid();
+
+  int lo = 0, hi = P.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.tile_start[mid] <= static_cast<int>(blockIdx.x)) lo = mid; else hi = mid - 1;
+  }
+  const JobDesc& J = P.job[lo];
+  if (P.step >= J.steps) return;
+
+  const int t = threadIdx.x;
+  const int lane = t & 31;
+  const int warp = t >> 5;
+  const int tile = static_cast<int>(blockIdx.x) - P.tile_start[lo];
+  const int n_v = J.n_v;
+  const int base = J.n_layers - 1;
+  const int cap = J.tile_cap;
+  const int par = (J.parity0 + P.step) & 1;
+  const FieldBuf in = J.buf[par];
+  const FieldBuf out = J.buf[par ^ 1];
+  const Coefs& c = J.c;
+  DevStatus* st = J.st;
+
+  Neighbourhood<DT> nb;
+  nb.rows = in.rows;
+  nb.Fid = in.ids;
+  nb.Fval = static_cast<const T*>(in.vals);
+  nb.Lcv = J.L_colval;
+  nb.dsum = 0.0f;
+  nb.p0 = nb.p1 = nb.q0 = nb.q1 = 0;
+#ifdef LF_CHECKED
+  nb.st = J.st;
+  nb.n_v = J.n_v;
+  nb.L_nnz = J.L_nnz;
+  nb.entries = J.num_tiles * J.tile_cap;
+#endif
+
+  const int i = tile * kBlock + t;
+  int4 h_own = make_int4(0, 0, 0, 0);
+  if (i < n_v) {
+    h_own = __ldg(in.head + i);
+    nb.q0 = __ldg(J.L_rowptr + i);
+    nb.q1 = __ldg(J.L_rowptr + i + 1);
+  }
+  if (t == 0) s_err = ld_relaxed_u32(&st->err);
+  __syncthreads();
+  if (s_err) return;                 // an earlier step of this job failed
+
+  const int own = h_own.x;
+  SlotMapT<K> mp;
+  mp.clear();
+  int own_cells = 0;
+  bool ok = true;
+  if (i < n_v) {
+    float gb = 0.0f, fb = 0.0f;
+    // the own row: the head record's two entries, the rest from the segment;
+    // its cells take the first slots (ids ascend, the base layer is last)
+    ok = own <= K;
+    int start = 0;
+    if (ok && own > 2) start = __ldg(nb.rows + i).x;
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      if (!ok || p >= own) continue;
+      int l;
+      float f;
+      if (p == 0) { l = h_own.y & 0xffff; f = V::from_bits(h_own.z); }
+      else if (p == 1) { l = (h_own.y >> 16) & 0xffff; f = V::from_bits(h_own.w); }
+      else { l = __ldg(nb.Fid + LF_CK(nb, start + p, nb.entries)); f = V::load(nb.Fval + LF_CK(nb, start + p, nb.entries)); }
+      if (l == base) {
+        fb = f;
+      } else {
+#pragma unroll
+        for (int s2 = 0; s2 < K - 1; ++s2)
+          if (s2 == own_cells) { mp.id[s2] = l; mp.f[s2] = f; }
+        ++own_cells;
+      }
+    }
+    ok = ok && own_cells <= K - 1;
+    ok = lean_gather(nb, in.head, base, mp, gb) && ok;
+    // the base layer joins the slots last (largest id)
+#pragma unroll
+    for (int s2 = 0; s2 < K; ++s2) {
+      if (s2 == mp.cnt) { mp.id[s2] = base; mp.g[s2] = gb; mp.f[s2] = fb; }
+    }
+    mp.cnt += 1;
+  }
+  // a tile with a vertex outside the shape takes the full step
+  if (!__syncthreads_and(ok)) {
+    step_tile<DT, false, false>(P);
+    return;
+  }
+
+  bool zero_sum = false;
+  int kept = 0, nsk = 0;
+  float vnew[K];
+  bool keep[K];
+#pragma unroll
+  for (int s2 = 0; s2 < K; ++s2) { vnew[s2] = 0.0f; keep[s2] = false; }
+  VertexSums S = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, 0};
+  float tot = 0.0f;
+  const GenCoef gc{};                // unused: class coefficients only
+  if (i < n_v) {
+    with_slots<K>(__reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
+      slot_update<DT, false, decltype(slots)::value>(mp, own_cells, own, nb.dsum, base, c, gc, false, S, vnew, keep,
+                                                     kept, tot, zero_sum);
+    });
+    nsk = S.nC + S.hasb;
+    if (zero_sum) kept = 0;
+  }
+
+  // ---- block scan of the output row lengths: offsets inside the segment ----
+  int x = kept;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  const unsigned sk = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(nsk));
+  if (lane == 31) {
+    s_warp_cnt[warp] = x;
+    s_red[warp] = sk;
+  }
+  const bool bad_sum = __syncthreads_or(zero_sum);
+  int warp_off = 0, tile_total = 0;
+  unsigned tile_sk = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    if (w < warp) warp_off += s_warp_cnt[w];
+    tile_total += s_warp_cnt[w];
+    tile_sk += s_red[w];
+  }
+  const int local_excl = warp_off + x - kept;
+
+  bool write = !bad_sum;
+  if (t == 0 && bad_sum) atomicOr(&st->err, ERR_ZERO_SUM);
+  if (write && tile_total > cap) {
+    write = false;
+    if (t == 0) {
+      atomicOr(&st->err, ERR_CAPACITY);
+      atomicMax(&st->need_tile, static_cast<unsigned long long>(tile_total));
+    }
+  }
+
+  // ---- write row i of the output, entries sorted by layer id ---------------
+  if (write && i < n_v) {
+    const int off = tile * cap + local_excl;
+    out.rows[i] = make_int2(off, kept);
+    T* ov = static_cast<T*>(out.vals);
+    int4 ho = make_int4(kept, 0, 0, 0);
+    auto put = [&](int o, int l, T vt) {
+#ifdef LF_CHECKED
+      const int w = tile * cap + nb.ck(o - tile * cap, cap);   // inside the tile's segment
+#else
+      const int w = o;
+#endif
+      out.ids[w] = static_cast<uint16_t>(l);
+      ov[w] = vt;
+      if (o == off) { ho.y = l; ho.z = V::bits(vt); }
+      else if (o == off + 1) { ho.y |= l << 16; ho.w = V::bits(vt); }
+    };
+    int top = 1;
+#pragma unroll
+    for (int s2 = 0; s2 < K; ++s2) top = keep[s2] ? s2 + 1 : top;
+    with_slots<K>(__reduce_max_sync(__activemask(), top), [&](auto slots) {
+      slot_write<DT, decltype(slots)::value>(mp, keep, vnew, off, put);
+    });
     out.head[i] = ho;
   }
 
@@ -1161,11 +1477,14 @@ __global__ void narrow_kernel(const float* __restrict__ src, void* __restrict__ 
 
 using StepFn = void (*)(const BatchParams);
 // [schedule][storage type]: the class-coefficient kernel at 4, 5 and 3 CTAs
-// per SM; the general-coefficient form keeps 4.
+// per SM, the register-tier kernel, and the kernel with the lean gather; the
+// general-coefficient form keeps 4.
 const StepFn kClassFns[kSchedules][3] = {
     {&step_kernel_impl<0, false, 4>, &step_kernel_impl<1, false, 4>, &step_kernel_impl<2, false, 4>},
     {&step_kernel_impl<0, false, 5>, &step_kernel_impl<1, false, 5>, &step_kernel_impl<2, false, 5>},
-    {&step_kernel_impl<0, false, 3>, &step_kernel_impl<1, false, 3>, &step_kernel_impl<2, false, 3>}};
+    {&step_kernel_impl<0, false, 3>, &step_kernel_impl<1, false, 3>, &step_kernel_impl<2, false, 3>},
+    {&step_kernel_hot<0>, &step_kernel_hot<1>, &step_kernel_hot<2>},
+    {&step_kernel_impl<0, false, 4, true>, &step_kernel_impl<1, false, 4, true>, &step_kernel_impl<2, false, 4, true>}};
 const StepFn kGeneralFns[3] = {&step_kernel_impl<0, true, 4>, &step_kernel_impl<1, true, 4>,
                                &step_kernel_impl<2, true, 4>};
 

@@ -1,9 +1,13 @@
 """The step-kernel schedules and the autotuner.
 
-The three schedules (the step kernel's registers allocated for 4, 5 and 3
-resident CTAs per SM) must give the same bits on every job, alone and in
-batches that mix them; the autotuner (lf_tune) advances the job like
-lf_step while it times them.
+The five schedules (the step kernel's registers allocated for 4, 5 and 3
+resident CTAs per SM; the lean register-tier path with the full step for
+the tiles outside its shape; the lean gather with the other tiers per
+vertex) must give the same bits on every job, alone and in batches that mix
+them; the autotuner (lf_tune) advances the job like lf_step while it times
+them.  The cases run through the first steps from the seeds, where most
+tiles are outside the lean path's shape, and a crowded mesh where many
+vertices stay outside it.
 """
 import numpy as np
 import pytest
@@ -47,7 +51,7 @@ def test_schedules_give_the_same_bits(lf, case):
     fac, k, sid, dt = CASES[case]
     m = fac()
     a = run(lf, m, k, sid, dt, "ctas4")
-    for other in ("ctas5", "ctas3"):
+    for other in ("ctas5", "ctas3", "hot", "lean"):
         b = run(lf, m, k, sid, dt, other)
         for fa, fb in zip(a[:-1], b[:-1]):
             for x, y in zip(fa, fb):
@@ -56,14 +60,14 @@ def test_schedules_give_the_same_bits(lf, case):
 
 
 def test_batch_mixing_schedules_matches_alone(lf):
-    ms = [c[0]() for c in CASES[:3]]
+    ms = [c[0]() for c in CASES]
     alone = []
-    for (fac, k, sid, dt), m in zip(CASES[:3], ms):
+    for (fac, k, sid, dt), m in zip(CASES, ms):
         alone.append(run(lf, m, k, sid, dt, "ctas4", steps=(150,))[0])
     meshes = []
-    for j, ((fac, k, sid, dt), m) in enumerate(zip(CASES[:3], ms)):
+    for j, ((fac, k, sid, dt), m) in enumerate(zip(CASES, ms)):
         x = lf.Mesh(m.V, m.F, field_dtype=dt)
-        x.set_schedule(["ctas5", "ctas4", "ctas3"][j])
+        x.set_schedule(["ctas5", "hot", "lean", "ctas3"][j])
         x.seed(synth.sample_seeds(m.n_v, k, sid))
         meshes.append(x)
     lf.lf_step_batch(meshes, 150)
@@ -79,14 +83,14 @@ def test_tune_advances_the_job_and_keeps_a_schedule(lf):
     with lf.Mesh(m.V, m.F) as a, lf.Mesh(m.V, m.F) as b:
         a.seed(seeds)
         b.seed(seeds)
-        s = a.tune(64)                     # two rounds over three schedules: 384 steps
-        assert s in (0, 1, 2) and a.schedule == s
-        assert a.stats()["steps"] == 384
-        b.step(384)
+        s = a.tune(64)                     # two rounds over five schedules: 640 steps
+        assert s in (0, 1, 2, 3, 4) and a.schedule == s
+        assert a.stats()["steps"] == 640
+        b.step(640)
         for x, y in zip(a.get_field(), b.get_field()):
             assert np.array_equal(x, y)
         with pytest.raises(lf.LFError):
-            a.set_schedule(3)
+            a.set_schedule(5)
         with pytest.raises(lf.LFError):
             a.tune(0)
     with lf.Mesh(m.V, m.F) as c:
