@@ -26,6 +26,7 @@ trace through lf_server: p50/p99 job latency), grid512_lloyd (Lloyd-like
 rounds and the dual mesh) and dt_sweep (the time step study).
 """
 import argparse
+import contextlib
 import hashlib
 import json
 import os
@@ -104,12 +105,16 @@ WORKLOADS = {
 # Counters of the step kernel from ncu captures (DRAM bytes and warp
 # instructions; steady state), valid only for the workload and the kernel
 # source they were taken on.
-NCU_COUNTERS = {"grid512": {"dtype": "f32", "kernel_sha": "f837f2781cf092bd",
-                             "bytes_per_launch": 17870080, "warp_instructions_per_launch": 11762763},
-                # one step of the batch with every job on schedule ctas4 (its FP32 and BF16
-                # launches, steps ~500 of 1000): DRAM read + write bytes and warp instructions
-                "batch64": {"kernel_sha": "f837f2781cf092bd", "measured_under": "every job on ctas4",
-                            "bytes_per_step": 956433408, "warp_instructions_per_step": 441048122}}
+# DRAM read + write bytes and warp instructions of the step kernel, from ncu
+# captures of the committed profile commands; keyed by workload, then by the
+# schedule every job ran under; void once the kernel source changes
+NCU_COUNTERS = {"kernel_sha": "b0b64229b4bbf4bf",
+                # launches 1001-1003 of the job (steps ~1000 of 2000)
+                "grid512": {"ctas4": {"bytes_per_launch": 17872299, "warp_instructions_per_launch": 11770155},
+                            "hot": {"bytes_per_launch": 17887403, "warp_instructions_per_launch": 13148319}},
+                # one batch step (FP32 launch + BF16 launch, steps ~490-515 of 1000)
+                "batch64": {"hot": {"bytes_per_step": 955717952, "warp_instructions_per_step": 495440220},
+                            "lean": {"bytes_per_step": 955072192, "warp_instructions_per_step": 486605608}}}
 SM_COUNT, SUBPARTITIONS = 152, 4          # GB300: 152 SMs, 4 schedulers each issuing one warp instruction a cycle
 L2_FLUSH_BYTES = 512 << 20
 
@@ -131,6 +136,18 @@ def measured_peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+@contextlib.contextmanager
+def profiled():
+    """The timed region as the profiler's capture range (cudaProfilerStart /
+    Stop; no effect without a profiler attached)."""
+    import torch
+    torch.cuda.profiler.start()
+    try:
+        yield
+    finally:
+        torch.cuda.profiler.stop()
 
 
 class ClockSampler:
@@ -347,6 +364,9 @@ def run_ours(args, wl):
     with torch.cuda.stream(stream):
         dev = lf.torch_device(stream)
         mesh = lf.Mesh(m.V, m.F, device=dev, field_dtype=wl["dtype"])
+        if args.schedule != "auto":
+            mesh.set_schedule(args.schedule)
+        sched = {v: k for k, v in lf.SCHEDULES.items()}[mesh.schedule]
         coefs = wl["coefs"](wl["k"] + 1) if wl.get("coefs") else None
         if coefs is not None:
             mesh.seed(seeds)
@@ -370,7 +390,7 @@ def run_ours(args, wl):
             dist.barrier()
         job_ms, step_ms, units, io, retries = [], [], 0, 0, 0
         wall0 = time.perf_counter()
-        with ClockSampler(local) as clk:
+        with ClockSampler(local) as clk, profiled():
             for _ in range(args.steps):
                 flush.zero_()                          # evict L2 between jobs
                 torch.cuda.synchronize()
@@ -406,15 +426,16 @@ def run_ours(args, wl):
     t_step = sum(step_ms) / 1e3
     achieved = bytes_total / t_step / 1e9
     peak, peak_kind = measured_peaks()
-    counters = NCU_COUNTERS.get(args.workload)
-    if counters and (counters["kernel_sha"] != kernel_sha() or wl["dtype"] != counters["dtype"]):
-        counters = None
+    counters = None
+    if NCU_COUNTERS["kernel_sha"] == kernel_sha() and wl["dtype"] == "f32" and wl.get("coefs") is None:
+        counters = NCU_COUNTERS.get(args.workload, {}).get(sched)
     traffic = counters["bytes_per_launch"] if counters else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_total / launches,
                 "us_per_launch": 1e6 * t_step / launches}
     if counters:
+        roofline["traffic_measured_under"] = f"schedule {sched}"
         # the bound that binds: instruction issue (ncu's warp-instruction count
         # per launch over the event-timed launch, against one warp instruction
         # per scheduler and cycle at the SM clock sampled during the run)
@@ -459,6 +480,7 @@ def run_ours(args, wl):
         "config": {"workload": args.workload, "desc": wl["desc"], "n_v": m.n_v, "n_f": m.n_f,
                    "seeds": wl["k"], "time_steps_per_job": T, "l2": "flushed between jobs (512 MiB write)",
                    "working_set_bytes": int(bytes_L + 2 * (4 * (m.n_v + 1) + (2 + vb) * st["capacity"])),
+                   "schedule": sched,
                    "lloyd_and_dual": "not part of this line"},
         "latency_ms": {"p50": float(np.percentile(job_ms, 50)), "p99": float(np.percentile(job_ms, 99))},
         "roofline": roofline,
@@ -552,7 +574,7 @@ def run_batch(args):
         if dist:
             dist.barrier()
         times, units, io, retries = [], 0, 0, 0
-        with ClockSampler(local) as clk:
+        with ClockSampler(local) as clk, profiled():
             for _ in range(args.steps):
                 seed_all()
                 times.append(timed(lambda: lf.lf_step_batch(meshes, T)))
@@ -564,7 +586,7 @@ def run_batch(args):
         if dist:
             dist.barrier()
         # the same batch under one fixed schedule for every job
-        fixed = {}
+        fixed, fixed_s = {}, {}
         for name in (() if args.timed_only else ("ctas4", "ctas5", "ctas3", "hot", "lean")):
             for mesh in meshes:
                 mesh.set_schedule(name)
@@ -573,6 +595,7 @@ def run_batch(args):
             seed_all()
             t_fixed = timed(lambda: lf.lf_step_batch(meshes, T))
             fixed[name] = sum(mesh.stats()["skeleton_total"] for mesh in meshes) / t_fixed
+            fixed_s[name] = t_fixed
         for mesh, sc in zip(meshes, tuned):
             mesh.set_schedule(sc)
         t_plain = units_plain = t_e2e = e2e_units = None
@@ -611,23 +634,30 @@ def run_batch(args):
     bytes_total = launches * bytes_step + io
     achieved = bytes_total / secs / 1e9
     peak, peak_kind = measured_peaks()
-    counters = NCU_COUNTERS.get("batch64")
-    if counters and counters["kernel_sha"] != kernel_sha():
-        counters = None
+    # DRAM traffic and instructions: captured with every job under one
+    # schedule; the line takes the schedule most jobs run under here
+    main = max(lf.SCHEDULES, key=lambda k: tuned.count(lf.SCHEDULES[k]))
+    counters = None
+    if NCU_COUNTERS["kernel_sha"] == kernel_sha():
+        counters = NCU_COUNTERS["batch64"].get(main)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": counters["bytes_per_step"] if counters else None, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_step": bytes_total / launches, "us_per_step": 1e6 * secs / launches,
                 "launches_per_step": len({(sp.dtype, sc) for sp, sc in zip(specs, tuned)})}
-    if counters:
-        roofline["traffic_measured_under"] = counters["measured_under"]
     clk_summary = clk.summary()
     if counters:
-        mhz = clk_summary.get("sm_mhz") or clk_summary.get("sm_max_mhz") or 2070.0
-        peak_issue = SM_COUNT * SUBPARTITIONS * mhz * 1e6
-        issued = counters["warp_instructions_per_step"] / (secs / launches)
-        roofline["issue"] = {"achieved": issued / 1e12, "peak": peak_issue / 1e12, "unit": "T warp-instr/s",
-                             "frac": issued / peak_issue,
-                             "warp_instructions_per_step": counters["warp_instructions_per_step"]}
+        roofline["traffic_measured_under"] = f"every job on {main} ({tuned.count(lf.SCHEDULES[main])} of " \
+                                             f"{len(tuned)} jobs here)"
+        if main in fixed_s:
+            # instruction issue of that batch: ncu's warp instructions per step
+            # over its event-timed step, against one warp instruction per
+            # scheduler and cycle at the SM clock sampled during the run
+            mhz = clk_summary.get("sm_mhz") or clk_summary.get("sm_max_mhz") or 2070.0
+            peak_issue = SM_COUNT * SUBPARTITIONS * mhz * 1e6
+            issued = counters["warp_instructions_per_step"] / (fixed_s[main] / T)
+            roofline["issue"] = {"achieved": issued / 1e12, "peak": peak_issue / 1e12, "unit": "T warp-instr/s",
+                                 "frac": issued / peak_issue, "under": f"every job on {main}",
+                                 "warp_instructions_per_step": counters["warp_instructions_per_step"]}
     n_v_total = sum(m.n_v for m in geo)
     config = {"workload": "batch64", "jobs": len(specs), "n_v_total": n_v_total,
               "time_steps_per_job": T, "bf16_jobs": sum(sp.dtype == "bf16" for sp in specs),
@@ -935,7 +965,8 @@ def main():
                     help="batch64: time the batch only, without the fixed-schedule, one-at-a-time and end-to-end "
                          "runs (the command the profiles capture)")
     ap.add_argument("--schedule", choices=["auto", "ctas4", "ctas5", "ctas3", "hot", "lean"], default="auto",
-                    help="batch64: the step-kernel schedule of every job (auto: lf_tune per job)")
+                    help="the step-kernel schedule of every job (auto: lf_tune per job in batch64, the "
+                         "default schedule ctas4 on the single-mesh workloads)")
     args = ap.parse_args()
     batch = args.workload == "batch64"
     if args.cpu_sample_steps is None:

@@ -397,6 +397,17 @@ __device__ __forceinline__ void with_slots(int n, Fn&& fn) {
   }
 }
 
+// As with_slots with three variants only (2, 4 or K slots): a lane does up
+// to one slot more work, and the kernel's warps share less code (the
+// register-tier kernel, which also holds the full step, lost issue slots to
+// instruction fetch with six variants).
+template <int K, class Fn>
+__device__ __forceinline__ void with_slots_coarse(int n, Fn&& fn) {
+  if (n <= 2) fn(std::integral_constant<int, 2>{});
+  else if (n <= 4) fn(std::integral_constant<int, 4>{});
+  else fn(std::integral_constant<int, K>{});
+}
+
 // Medium path: a map of kMed slots in shared memory, one of kPool per CTA,
 // taken by the (rare) threads whose union outgrows the register map.
 struct MedMap {
@@ -1267,7 +1278,7 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_hot(const __grid_consta
   float tot = 0.0f;
   const GenCoef gc{};                // unused: class coefficients only
   if (i < n_v) {
-    with_slots<K>(__reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
+    with_slots_coarse<K>(__reduce_max_sync(__activemask(), mp.cnt), [&](auto slots) {
       slot_update<DT, false, decltype(slots)::value>(mp, own_cells, own, nb.dsum, base, c, gc, false, S, vnew, keep,
                                                      kept, tot, zero_sum);
     });
@@ -1328,7 +1339,7 @@ __global__ void __launch_bounds__(kBlock, 4) step_kernel_hot(const __grid_consta
     int top = 1;
 #pragma unroll
     for (int s2 = 0; s2 < K; ++s2) top = keep[s2] ? s2 + 1 : top;
-    with_slots<K>(__reduce_max_sync(__activemask(), top), [&](auto slots) {
+    with_slots_coarse<K>(__reduce_max_sync(__activemask(), top), [&](auto slots) {
       slot_write<DT, decltype(slots)::value>(mp, keep, vnew, off, put);
     });
     out.head[i] = ho;
