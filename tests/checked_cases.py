@@ -34,10 +34,12 @@ def run_cases(out):
         res[name + "_stats"] = np.array([st["skeleton_total"], st["nnz_io_total"], st["retries"]], np.int64)
 
     g = synth.planar_grid(61, seed=2)
-    with lf.Mesh(g.V, g.F) as mesh:                                    # register tier, ragged last tile
-        mesh.seed(synth.sample_seeds(g.n_v, 64, 3))
-        mesh.step(300)
-        keep("grid", mesh)
+    for sched in ("ctas4", "hot", "lean"):                             # register tier, ragged last tile
+        with lf.Mesh(g.V, g.F) as mesh:                                # (and the lean schedules' gather)
+            mesh.set_schedule(sched)
+            mesh.seed(synth.sample_seeds(g.n_v, 64, 3))
+            mesh.step(300)
+            keep("grid" if sched == "ctas4" else f"grid_{sched}", mesh)
     t = synth.noisy_torus(40)
     with lf.Mesh(t.V, t.F, field_dtype="bf16", initial_capacity=t.n_v) as mesh:   # growth and re-runs
         mesh.seed(synth.sample_seeds(t.n_v, 32, 5))
@@ -45,17 +47,25 @@ def run_cases(out):
         keep("torus_bf16", mesh)
     small = synth.planar_grid(20, seed=6)
     for per_row, n_layers in ((5, 200), (14, 400)):                    # shared-memory and storage-free tiers
-        rng = np.random.default_rng(per_row)
-        with lf.Mesh(small.V, small.F) as mesh:
-            mesh.set_field(*random_field(small.n_v, n_layers, per_row, rng), n_layers)
-            mesh.step(1)
-            keep(f"unions{per_row}", mesh)
+        for sched in ("ctas4", "hot", "lean"):                         # (hot: every tile takes the full step)
+            rng = np.random.default_rng(per_row)
+            with lf.Mesh(small.V, small.F) as mesh:
+                mesh.set_schedule(sched)
+                mesh.set_field(*random_field(small.n_v, n_layers, per_row, rng), n_layers)
+                mesh.step(1)
+                keep(f"unions{per_row}" + ("" if sched == "ctas4" else f"_{sched}"), mesh)
     meshes = [lf.Mesh(m.V, m.F, field_dtype=d) for m, d in ((g, "f32"), (t, "bf16"), (synth.icosphere(3), "f16"))]
     for k, mesh in enumerate(meshes):
         mesh.seed(synth.sample_seeds(mesh.n_v, 16 + 8 * k, 7 + k))
     lf.lf_step_batch(meshes, [150, 90, 120])                           # one launch per step and storage type
     for k, mesh in enumerate(meshes):
         keep(f"batch{k}", mesh)
+    for k, (mesh, sched) in enumerate(zip(meshes, ("hot", "lean", "hot"))):
+        mesh.set_schedule(sched)                                       # the lean schedules in a batch
+        mesh.seed(synth.sample_seeds(mesh.n_v, 16 + 8 * k, 7 + k))
+    lf.lf_step_batch(meshes, [150, 90, 120])
+    for k, mesh in enumerate(meshes):
+        keep(f"batch{k}_lean", mesh)
         mesh.close()
     rng = np.random.default_rng(11)
     mats = [0.2 * rng.random((31, 31)) for _ in range(3)]

@@ -4,9 +4,10 @@ compute-sanitizer is not available to these tests, so the library has a
 checked build of its own: every index the step kernel reads or writes
 through is compared with its array's length, and one outside raises an error
 bit instead of leaving the buffer.  The same cases (every tier of the step
-kernel, growth with re-runs, all three storage types, a batch, general
-coefficient matrices, region seeds) run in a child process against each
-build: no case may raise the error, and every result must be bit-identical.
+kernel, under the default schedule and the two lean ones, growth with
+re-runs, all three storage types, batches, general coefficient matrices,
+region seeds) run in a child process against each build: no case may raise
+the error, and every result must be bit-identical.
 Then an operator entry one past the last vertex, given to the checked build
 alone, must come back as an error status, not as a memory fault.
 """
@@ -42,6 +43,10 @@ def test_checked_build_finds_no_bad_index_and_gives_the_same_bits(tmp_path):
     for k in a.files:
         assert a[k].dtype == b[k].dtype and np.array_equal(a[k], b[k]), k
     assert a["torus_bf16_stats"][2] > 0                  # the growth path ran
+    for k in a.files:                                    # the schedules give the same bits
+        for sched in ("_hot", "_lean"):                  # (retries depend on the capacity left by earlier runs)
+            if sched in k and not k.endswith("_stats"):
+                assert np.array_equal(a[k], a[k.replace(sched, "")]), k
 
 
 def test_checked_build_reports_an_index_past_the_end():
