@@ -559,7 +559,7 @@ def run_batch(args):
         if args.schedule == "auto":
             for mesh, sd in zip(meshes, seeds):
                 mesh.seed(sd)
-                mesh.step(TUNE_AT)
+                mesh.step(args.tune_at)
                 mesh.tune(TUNE_TRIAL)
         else:
             for mesh in meshes:
@@ -679,7 +679,7 @@ def run_batch(args):
         "schedules": {("tuned" if args.schedule == "auto" else args.schedule): units / secs,
                       **{f"all_{k}": v for k, v in fixed.items()}, "unit": UNIT,
                       "jobs": {k: tuned.count(v) for k, v in lf.SCHEDULES.items()}, "tune_s": t_tune,
-                      "desc": f"per job, lf_tune after {TUNE_AT} steps ({TUNE_TRIAL} steps per schedule and round, "
+                      "desc": f"per job, lf_tune after {args.tune_at} steps ({TUNE_TRIAL} steps per schedule and round, "
                               "two rounds) picks the step kernel's register allocation for 4, 5 or 3 CTAs per SM, "
                               "the lean register-tier path with the full step for the tiles outside it, or the lean gather with "
                               "the other tiers per vertex (same bits); the "
@@ -961,6 +961,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--order", choices=["generated", "locality"], default="generated",
                     help="batch64: the meshes' vertex numbering (locality: renumbered before lf_create_mesh)")
+    ap.add_argument("--tune-at", type=int, default=TUNE_AT,
+                    help="batch64: steps from the seeds before lf_tune's trials")
     ap.add_argument("--timed-only", action="store_true",
                     help="batch64: time the batch only, without the fixed-schedule, one-at-a-time and end-to-end "
                          "runs (the command the profiles capture)")
