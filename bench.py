@@ -107,7 +107,9 @@ WORKLOADS = {
 # source they were taken on.
 # DRAM read + write bytes and warp instructions of the step kernel, from ncu
 # captures of the committed profile commands; keyed by workload, then by the
-# schedule every job ran under; void once the kernel source changes
+# schedule every job ran under; void once the kernel source changes (the line
+# then reports null traffic, with these figures beside it as an earlier
+# source's)
 NCU_COUNTERS = {"kernel_sha": "b0b64229b4bbf4bf",
                 # launches 1001-1003 of the job (steps ~1000 of 2000)
                 "grid512": {"ctas4": {"bytes_per_launch": 17872299, "warp_instructions_per_launch": 11770155},
@@ -434,6 +436,11 @@ def run_ours(args, wl):
                 "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_total / launches,
                 "us_per_launch": 1e6 * t_step / launches}
+    stale = NCU_COUNTERS.get(args.workload, {}).get(sched) if NCU_COUNTERS["kernel_sha"] != kernel_sha() else None
+    if stale and wl["dtype"] == "f32" and wl.get("coefs") is None:
+        # counters of an earlier kernel source: stated beside the null, not as the traffic
+        roofline["traffic_earlier_source"] = {"bytes_per_launch": stale["bytes_per_launch"],
+                                              "kernel_sha": NCU_COUNTERS["kernel_sha"], "current_sha": kernel_sha()}
     if counters:
         roofline["traffic_measured_under"] = f"schedule {sched}"
         # the bound that binds: instruction issue (ncu's warp-instruction count
@@ -645,6 +652,11 @@ def run_batch(args):
                 "algorithmic_bytes_per_step": bytes_total / launches, "us_per_step": 1e6 * secs / launches,
                 "launches_per_step": len({(sp.dtype, sc) for sp, sc in zip(specs, tuned)})}
     clk_summary = clk.summary()
+    stale = NCU_COUNTERS["batch64"].get(main) if NCU_COUNTERS["kernel_sha"] != kernel_sha() else None
+    if stale:
+        # counters of an earlier kernel source: stated beside the null, not as the traffic
+        roofline["traffic_earlier_source"] = {"bytes_per_step": stale["bytes_per_step"], "under": f"every job on {main}",
+                                              "kernel_sha": NCU_COUNTERS["kernel_sha"], "current_sha": kernel_sha()}
     if counters:
         roofline["traffic_measured_under"] = f"every job on {main} ({tuned.count(lf.SCHEDULES[main])} of " \
                                              f"{len(tuned)} jobs here)"

@@ -525,7 +525,8 @@ __device__ __forceinline__ void slot_write(const SlotMapT<K>& mp, const bool (&k
 // Each layer's sum runs in the row order of L, as on every other path.  The
 // sum of the row's off-diagonal weights goes to nb.dsum.  False when a cell
 // found no free slot (one stays for the base layer); the map is then
-// incomplete and only nb.dsum is final.  mp.cnt: the cells in the map.
+// incomplete and only nb.dsum is final.  mp.cnt: the cells in the map (all K
+// slots counted).
 template <int DT, int K>
 __device__ __forceinline__ bool lean_gather(Neighbourhood<DT>& nb, const int4* __restrict__ head, const int base,
                                             SlotMapT<K>& mp, float& gB) {
@@ -589,9 +590,11 @@ __device__ __forceinline__ bool lean_gather(Neighbourhood<DT>& nb, const int4* _
       }
     }
   }
+  // every slot counts: an own row of K cells and no base entry fills the
+  // last slot too, and the caller must see K (no room left for the base)
   int n = 0;
 #pragma unroll
-  for (int s2 = 0; s2 < K - 1; ++s2) n += mp.id[s2] >= 0;
+  for (int s2 = 0; s2 < K; ++s2) n += mp.id[s2] >= 0;
   mp.cnt = n;
   return fit;
 }

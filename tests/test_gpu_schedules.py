@@ -59,6 +59,51 @@ def test_schedules_give_the_same_bits(lf, case):
         assert a[-1] == b[-1]
 
 
+def full_rows_field(m, cells, specials):
+    """Every vertex holds cell 0 (0.9) and the base layer (0.1); each vertex of
+    specials holds `cells` cells (0, 1, ...) in equal parts and no base entry.
+    Its neighbours bring no cell it lacks, so a register map that has room
+    for `cells` cells keeps it on its fastest tier to the end of the gather."""
+    base = cells + 2
+    rp, ids, vals = [0], [], []
+    for v in range(m.n_v):
+        if v in specials:
+            ids += list(range(cells))
+            vals += [1.0 / cells] * cells
+        else:
+            ids += [0, base]
+            vals += [0.9, 0.1]
+        rp.append(len(ids))
+    return (np.array(rp, np.int64), np.array(ids, np.int32), np.array(vals, np.float32)), base + 1
+
+
+@pytest.mark.parametrize("cells", [4, 5, 6])
+def test_full_own_rows_on_every_schedule(lf, oracle_mod, cells):
+    """Own rows of as many cells as a register map has slots (five slots at
+    4 CTAs per SM, six in the lean forms) and no base entry: the base layer
+    must not take a cell's slot.  One step on every schedule, bit for bit,
+    and against the oracle."""
+    from parity_util import ambiguous_rows, check_compare, compare, field_from_lib
+    m = synth.planar_grid(16, seed=4)
+    specials = {5 * 16 + 5, 8 * 16 + 9, 10 * 16 + 4}
+    state, n_layers = full_rows_field(m, cells, specials)
+    got = {}
+    for sched in lf.SCHEDULES:
+        with lf.Mesh(m.V, m.F) as mesh:
+            mesh.set_schedule(sched)
+            mesh.set_field(*state, n_layers)
+            mesh.step(1)
+            got[sched] = mesh.get_field()
+    for sched, f in got.items():
+        for x, y in zip(f, got["ctas4"]):
+            assert np.array_equal(x, y), sched
+    rp, ids, vals = got["ctas4"]
+    L = oracle_mod.cotan_laplacian(m.V, m.F)
+    Fin = oracle_mod.Field(state[0], state[1], state[2].astype(np.float64), n_layers)
+    Fo, _, mg = oracle_mod.step(L, Fin, margins=True)
+    check_compare(compare(Fo, field_from_lib(rp, ids, vals, n_layers, oracle_mod), ambiguous_rows(mg), oracle_mod))
+
+
 def test_batch_mixing_schedules_matches_alone(lf):
     ms = [c[0]() for c in CASES]
     alone = []
