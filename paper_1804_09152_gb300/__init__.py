@@ -17,7 +17,9 @@ A tessellation with Lloyd-like rounds and its dual mesh::
         triangles = mesh.extract_dual()      # dual mesh over the seed vertices
 
 Many meshes at once: ``lf.lf_step_batch([m0, m1, ...], counts)``; a stream of
-jobs under a memory budget: ``lf.Server``.
+jobs under a memory budget: ``lf.Server``.  ``mesh.tune(32)`` times the step
+kernel's five schedules on the job itself and keeps the fastest (they give the
+same bits); ``mesh.set_schedule("hot")`` fixes one.
 """
 from .native import build, LIB
 
